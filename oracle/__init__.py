@@ -1,0 +1,271 @@
+"""FP64 CPU oracle for the SQNGD hot path (ctypes wrapper around sqngd_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` are the only
+callers.  The product package never imports this module, and this module
+imports nothing from the product package.
+
+Conventions (same as the C file): complex arrays are numpy complex128 of shape
+[M, N]; the ambiguity grid is [M, M, D, L] with pair (m, l) = (transmit m,
+receive filter l), d = k - k_lo; weights are [D, L] or None (w = 1/N).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sqngd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no target-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
+    return _lib
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_longlong)
+
+
+def _d(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _grid(nu, k_lo, k_hi, weights):
+    nu = _f64(nu)
+    w = None if weights is None else _f64(weights)
+    if w is not None:
+        assert w.shape == (k_hi - k_lo + 1, nu.size)
+    return nu, w
+
+
+# ---------------------------------------------------------------- Eq. 6
+def ambiguity(x, h, nu, k_lo, k_hi):
+    """Full grid chi[m, l, d, j] (Eq. 6, n counted from 0)."""
+    x, h = _c128(x), _c128(h)
+    M, N = x.shape
+    nu = _f64(nu)
+    D = k_hi - k_lo + 1
+    out = np.zeros((M, M, D, nu.size), dtype=np.complex128)
+    lib().or_ambiguity(M, N, nu.size, _d(nu), k_lo, k_hi, _d(x), _d(h), _d(out))
+    return out
+
+
+def ambiguity_cells(x, h, nu, k_lo, k_hi, cells):
+    """chi at the given linear cell indices ((m*M + l)*D + d)*L + j."""
+    x, h = _c128(x), _c128(h)
+    M, N = x.shape
+    nu = _f64(nu)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.zeros(cells.size, dtype=np.complex128)
+    lib().or_ambiguity_cells(M, N, nu.size, _d(nu), k_lo, k_hi, _d(x), _d(h),
+                             int(cells.size), cells.ctypes.data_as(_lp), _d(out))
+    return out
+
+
+# ---------------------------------------------------------------- loss, Eqs. 7-9, 37-42
+def loss(x, h, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, pnorm=0.0):
+    """Returns dict(loss, wpsl, wapsl, wcpsl, snrl_term, cls, p[M], cells[2])."""
+    x, h = _c128(x), _c128(h)
+    M, N = x.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    terms = np.zeros(6)
+    p = np.zeros(M)
+    cells = np.zeros(2, dtype=np.int64)
+    lib().or_loss(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                  ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(x), _d(h),
+                  _d(terms), _d(p), cells.ctypes.data_as(_lp))
+    return dict(loss=terms[0], wpsl=terms[1], wapsl=terms[2], wcpsl=terms[3],
+                snrl_term=terms[4], cls=int(terms[5]), p=p, cells=cells)
+
+
+def grad_xh(x, h, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, pnorm=0.0,
+            use_cell=None):
+    """Analytic gradient (dL/dRe + j dL/dIm) w.r.t. x and h; returns (terms, gx, gh)."""
+    x, h = _c128(x), _c128(h)
+    M, N = x.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    terms = np.zeros(6)
+    gx = np.zeros_like(x)
+    gh = np.zeros_like(h)
+    uc = None
+    if use_cell is not None:
+        uc = (ctypes.c_longlong * 1)(int(use_cell))
+    lib().or_grad_xh(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                     ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(x), _d(h),
+                     uc, _d(terms), _d(gx), _d(gh))
+    return terms, gx, gh
+
+
+# ---------------------------------------------------------------- quantizers, Eqs. 24, 25, 43
+def thresholds(B, r_n):
+    K = B * r_n
+    rho = np.zeros(K)
+    a = ctypes.c_double(0)
+    lib().or_thresholds(B, r_n, _d(rho), ctypes.byref(a))
+    return rho, a.value
+
+
+def soft_quantize(z, rho, a, c):
+    z = _f64(z).ravel()
+    rho = _f64(rho)
+    y = np.zeros_like(z)
+    dy = np.zeros_like(z)
+    lib().or_soft_quantize(z.size, _d(z), rho.size, _d(rho), ctypes.c_double(a),
+                           ctypes.c_double(c), _d(y), _d(dy))
+    return y, dy
+
+
+def hard_quantize(z, rho, B):
+    z = _f64(z).ravel()
+    rho = _f64(rho)
+    q = np.zeros(z.size, dtype=np.int32)
+    b = np.zeros(z.size, dtype=np.int32)
+    lib().or_hard_quantize(z.size, _d(z), rho.size, _d(rho), B,
+                           q.ctypes.data_as(_ip), b.ctypes.data_as(_ip))
+    return q, b
+
+
+def hard_quantize_literal(z, rho, a, c):
+    z = _f64(z).ravel()
+    rho = _f64(rho)
+    y = np.zeros_like(z)
+    lib().or_hard_quantize_literal(z.size, _d(z), rho.size, _d(rho), ctypes.c_double(a),
+                                   ctypes.c_double(c), _d(y))
+    return y
+
+
+# ---------------------------------------------------------------- projection, Adam
+def project(h):
+    h = _c128(h).copy()
+    M, N = h.shape
+    lib().or_project(M, N, _d(h))
+    return h
+
+
+def adam(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place on float64 arrays theta, m, v."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(g)
+    lib().or_adam(theta.size, _d(theta), _d(g), _d(m), _d(v), ctypes.c_longlong(t),
+                  ctypes.c_double(lr), ctypes.c_double(b1), ctypes.c_double(b2),
+                  ctypes.c_double(eps))
+
+
+# ---------------------------------------------------------------- transmit chain
+def soft_waveform(u, rho, a, c):
+    u = _f64(u)
+    M, N = u.shape
+    x = np.zeros((M, N), dtype=np.complex128)
+    dy = np.zeros((M, N))
+    lib().or_soft_waveform(M, N, _d(u), rho.size, _d(_f64(rho)), ctypes.c_double(a),
+                           ctypes.c_double(c), _d(x), _d(dy))
+    return x, dy
+
+
+def hard_waveform(u, rho, B):
+    u = _f64(u)
+    M, N = u.shape
+    x = np.zeros((M, N), dtype=np.complex128)
+    q = np.zeros((M, N), dtype=np.int32)
+    lib().or_hard_waveform(M, N, _d(u), rho.size, _d(_f64(rho)), B, q.ctypes.data_as(_ip), _d(x))
+    return q, x
+
+
+def loss_grad_u(u, h, rho, a, c, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5,
+                pnorm=0.0, use_cell=None):
+    """Loss and gradient w.r.t. the logits u and the filters h (soft waveform)."""
+    u = _f64(u)
+    h = _c128(h)
+    M, N = u.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    terms = np.zeros(6)
+    gu = np.zeros((M, N))
+    gh = np.zeros((M, N), dtype=np.complex128)
+    uc = None
+    if use_cell is not None:
+        uc = (ctypes.c_longlong * 1)(int(use_cell))
+    lib().or_loss_grad_u(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                         ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(u),
+                         rho.size, _d(_f64(rho)), ctypes.c_double(a), ctypes.c_double(c),
+                         _d(h), uc, _d(terms), _d(gu), _d(gh))
+    return terms, gu, gh
+
+
+def sqngd_outer(state, cfg):
+    """One outer iteration of Algorithm 1; state is a dict of float64 arrays
+    (u, h, mu, vu, mh, vh) and counters (t_x, t_h), updated in place."""
+    M, N = state["u"].shape
+    nu, w = _grid(cfg["nu"], cfg["k_lo"], cfg["k_hi"], cfg.get("weights"))
+    rho = _f64(cfg["rho"])
+    n_ev = cfg["n_h"] + cfg["n_x"]
+    losses = np.zeros(n_ev)
+    wpsl = np.zeros(n_ev)
+    tx = ctypes.c_longlong(state["t_x"])
+    th = ctypes.c_longlong(state["t_h"])
+    hv = state["h"].view(np.float64)
+    lib().or_sqngd_outer(
+        M, N, nu.size, _d(nu), cfg["k_lo"], cfg["k_hi"], _d(w), ctypes.c_double(cfg["eps"]),
+        ctypes.c_double(cfg["snrl_db"]), ctypes.c_double(cfg.get("pnorm", 0.0)),
+        cfg["B"], rho.size, _d(rho), ctypes.c_double(cfg["a"]), ctypes.c_double(cfg["c"]),
+        cfg["n_h"], cfg["n_x"], ctypes.c_double(cfg["lr_h"]), ctypes.c_double(cfg["lr_x"]),
+        ctypes.c_double(cfg.get("b1", 0.9)), ctypes.c_double(cfg.get("b2", 0.999)),
+        ctypes.c_double(cfg.get("adam_eps", 1e-8)),
+        _d(state["u"]), _d(hv), _d(state["mu"]), _d(state["vu"]),
+        _d(state["mh"].view(np.float64)), _d(state["vh"].view(np.float64)),
+        ctypes.byref(tx), ctypes.byref(th), _d(losses), _d(wpsl))
+    state["t_x"] = tx.value
+    state["t_h"] = th.value
+    return losses, wpsl
+
+
+def metrics(x, h, nu, k_lo, k_hi, weights=None):
+    """(APSL dB, CPSL dB, PSLR dB, max SNRL dB) and per-waveform SNRL (Eqs. 10, 48)."""
+    x, h = _c128(x), _c128(h)
+    M, N = x.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    out = np.zeros(4)
+    snrl = np.zeros(M)
+    lib().or_metrics(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), _d(x), _d(h), _d(out), _d(snrl))
+    return out, snrl
+
+
+def init_logits(b, B, r_n):
+    """Initial logits for phase indices b (middle copy of the K = B*r_n
+    quantization regions, so the hard quantizer returns q = r_n//2 * B + b)."""
+    K = B * r_n
+    z0 = ((r_n // 2) * B + np.asarray(b, dtype=np.float64)) / K
+    return np.log(z0 / (1.0 - z0))
