@@ -1,0 +1,393 @@
+"""Throughput of the SQNGD hot path on GB300: AF/CAF loss+grad evaluations/s.
+
+One step = one outer iteration of Algorithm 1 on the mid-size problem (M=4
+waveforms, N=512 chips, B=16 phase levels, every delay |k| <= 511, 512
+Doppler bins over [-0.5, 0.5) cycles/chip): 10 loss+grad evaluations with
+Adam + projection on the filters, then 10 through the soft quantizer with
+Adam on the logits, replayed as one CUDA graph by sqngd_step.  value =
+evaluations per second over all ranks.  Every rank optimises its own seeded
+design (independent problems, no data-path collective; weak scaling).
+
+--impl reference times the FP64 CPU oracle on the same workload (one
+loss+grad evaluation per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "AF/CAF loss+grad evals/s"
+UNIT = "evals/s"
+PROFILES = os.path.join(ROOT, "profiles")
+FWD_SOURCES = ["paper_2604_25728_gb300/csrc/af_fft.cu", "paper_2604_25728_gb300/csrc/af_common.cuh",
+               "paper_2604_25728_gb300/csrc/af_kernels.h"]
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    from paper_2604_25728_gb300 import workloads as wl
+    return wl.mid()
+
+
+def _config(w, extra=None):
+    cfg = {"workload": w.name + ": one SQNGD outer iteration (10 filter + 10 transmit loss+grad evals) per step",
+           "M": w.M, "N": w.N, "B": w.B, "L": w.L, "delays": w.D, "r_n": w.r_n, "c": w.c, "eps": w.eps,
+           "snrl_db": w.snrl_db, "evals_per_step": w.n_h + w.n_x,
+           "l2": "flushed between timed steps (256 MiB memset outside each step's events)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- roofline --
+def _fwd_flops(w) -> float:
+    """Algorithmic FLOPs of one fused forward launch on the FFT grid:
+    6 per valid lag product (complex multiply by a conjugate), 5 L log2 L per
+    (pair, delay) row for the L-point transform, 3 per cell for |chi|^2."""
+    P = w.M * w.M
+    n = np.arange(w.k_lo, w.k_hi + 1)
+    valid = np.clip(w.N - np.abs(n), 0, None).sum()
+    rows = P * w.D
+    return 6.0 * P * valid + rows * 5.0 * w.L * np.log2(w.L) + 3.0 * rows * w.L
+
+
+def _fp32_peak_tflops() -> tuple[float, str]:
+    # 152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2.070 GHz maximum SM clock
+    return 152 * 128 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+
+
+def _source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record(kernel_hash: str):
+    path = os.path.join(PROFILES, "fwd_fft_mid_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_hash:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------- oracle ----
+def _oracle_sample(w, seed: int, budget_s: float):
+    """The FP64 oracle on the same workload: loss+grad evaluations (alternating
+    filter and transmit steps) until the time budget is spent."""
+    import oracle as orc
+    from paper_2604_25728_gb300 import workloads as wl
+    rho, a = orc.thresholds(w.B, w.r_n)
+    b = wl.phase_indices(seed, w.M, w.N, w.B)
+    u = orc.init_logits(b, w.B, w.r_n)
+    h = orc.project(np.exp(2j * np.pi * b / w.B))
+    st = dict(u=u, h=h, mu=np.zeros_like(u), vu=np.zeros_like(u), mh=np.zeros_like(h), vh=np.zeros_like(h),
+              t_x=0, t_h=0)
+    cfg = dict(nu=w.nu, k_lo=w.k_lo, k_hi=w.k_hi, eps=w.eps, snrl_db=w.snrl_db, B=w.B, rho=rho, a=a, c=w.c,
+               n_h=1, n_x=1, lr_h=w.lr_h, lr_x=w.lr_x)
+    evals = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.sqngd_outer(st, cfg)
+        evals += 2
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return evals, dt
+
+
+def _cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------- arms ------
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = _workload()
+    import oracle as orc
+    orc.build()
+    for _ in range(args.warmup):
+        _oracle_sample(w, 0, 0.0)
+    t0 = time.perf_counter()
+    evals = 0
+    for _ in range(args.steps):
+        e, _ = _oracle_sample(w, 0, 0.0)
+        evals += e
+    dt = time.perf_counter() - t0
+    v = evals / dt
+    cores = _cores()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": _config(w, {"reference": "FP64 CPU oracle (direct O(M^2 N^2 L) sums, OpenMP), "
+                                                "one filter step + one transmit step per step",
+                                  "l2": "n/a (CPU)"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} steps x 2 loss+grad evaluations of the full workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2604_25728_gb300 import api
+    from paper_2604_25728_gb300 import workloads as wl
+
+    w = _workload()
+    seed = rank
+    ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                      n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x)
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(wl.phase_indices(seed, w.M, w.N, w.B)).to(dev)
+    u, h = ctx.sqngd_init(b)
+    st = api.SqngdState.create(u, h)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evals_per_step = w.n_h + w.n_x
+
+    for _ in range(args.warmup):
+        ctx.sqngd_step(st, 1, log=False)
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-timed steps -------------------------------------------------
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        ev0[i].record(stream)
+        ctx.sqngd_step(st, 1, log=False)
+        ev1[i].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ctx.af_sync()
+    step_ms = np.array([a.elapsed_time(z) for a, z in zip(ev0, ev1)])
+    total_s = step_ms.sum() / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = K * evals_per_step * ws / total_s
+
+    # ---- dominant kernel alone: the fused forward pass ------------------------
+    R = 200
+    xh = torch.empty((w.M, w.N), dtype=torch.complex64, device=dev)
+    ctx.quantize(torch.sigmoid(st.u), x=xh)
+    fe0 = torch.cuda.Event(enable_timing=True)
+    fe1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(10):
+        ctx.af_forward(xh, st.h)
+    torch.cuda.synchronize()
+    fwd_ms = []
+    for _ in range(R):
+        fe0.record(stream)
+        ctx.af_forward(xh, st.h)
+        fe1.record(stream)
+        fe1.synchronize()
+        fwd_ms.append(fe0.elapsed_time(fe1))
+    fwd_s = float(np.mean(fwd_ms)) / 1e3
+    flops = _fwd_flops(w)
+    peak, peak_note = _fp32_peak_tflops()
+    achieved = flops / fwd_s / 1e12
+    khash = _source_hash(FWD_SOURCES)
+    traffic = _traffic_record(khash)
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    pin_u = torch.empty((w.M, w.N), dtype=torch.float32).pin_memory()
+    pin_h = torch.empty((w.M, w.N), dtype=torch.complex64).pin_memory()
+    pin_u.copy_(st.u.cpu())
+    pin_h.copy_(st.h.cpu())
+    out_u = torch.empty_like(pin_u).pin_memory()
+    out_h = torch.empty_like(pin_h).pin_memory()
+    Ke = max(10, K // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    log_bytes = evals_per_step * 4 * 8
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = []
+    for _ in range(Ke):
+        e0.record(stream)
+        st.u.copy_(pin_u, non_blocking=True)
+        st.h.copy_(pin_h, non_blocking=True)
+        ctx.sqngd_step(st, 1, log=True)           # synchronous: reads the step's loss log back
+        out_u.copy_(st.u, non_blocking=True)
+        out_h.copy_(st.h, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        pin_u.copy_(out_u)
+        pin_h.copy_(out_h)
+        flush.zero_()
+    e2e_s = float(np.sum(e2e_ms)) / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = Ke * evals_per_step * ws / e2e_s
+    h2d = pin_u.numel() * 4 + pin_h.numel() * 8
+    d2h = out_u.numel() * 4 + out_h.numel() * 8 + log_bytes
+
+    best = st.best.cpu().numpy()
+    acc = ctx.af_eval_hard(st.u, st.h)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        evals, dt = _oracle_sample(w, seed, 12.0)
+        cpu = {"value": evals / dt, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+               "sample": f"{evals} loss+grad evaluations (alternating filter/transmit Adam steps) of the same "
+                         f"workload, {dt:.1f} s of FP64 CPU work"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(w, {"seed_per_rank": "rank", "path": "FFT (AF_PATH_FFT)"}),
+            "roofline": {"bound": "alu", "kernel": "fwd_fft_kernel<512> (af_forward)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_note,
+                         "algorithmic_flops_per_launch": flops, "launch_us": fwd_s * 1e6,
+                         "traffic": traffic, "kernel_source_hash": khash},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            # per sqngd_step call: counters, best-record copy in, hard waveform,
+            # the graph (forward + finish per evaluation), best-record copy out
+            "gpu_launches": K * (2 * evals_per_step + 4),
+            "clocks": clocks,
+            "quality": {"best_hard_wpsl_db": float(20 * np.log10(best[0])) if np.isfinite(best[0]) else None,
+                        "final_pslr_db_fp64": float(acc[2]), "final_max_snrl_db": float(acc[3]),
+                        "outer_iterations": int(st.outer)},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,28 @@ static cplx af_cell(int N, const cplx* xm, const cplx* hl, int k, double nu)
     return s;
 }
 
+/* The same sum with the phasors e^{j 2 pi nu n} of one Doppler bin taken
+ * from a table row e[n] = phasor(nu n) (built once per call). */
+static cplx af_cell_tab(int N, const cplx* xm, const cplx* hl, int k, const cplx* e)
+{
+    cplx s = 0.0;
+    for (int n = 0; n < N; ++n) {
+        int p = n + k;
+        if (p < 0 || p >= N) continue;
+        s += xm[n] * conj(hl[p]) * e[n];
+    }
+    return s;
+}
+
+/* Table E[j][n] = phasor(nu_j n). */
+static cplx* phasor_table(int N, int L, const double* nu)
+{
+    cplx* e = (cplx*)malloc(sizeof(cplx) * (size_t)N * L);
+    for (int j = 0; j < L; ++j)
+        for (int n = 0; n < N; ++n) e[(size_t)j * N + n] = phasor(nu[j] * (double)n);
+    return e;
+}
+
 void or_ambiguity(int M, int N, int L, const double* nu, int k_lo, int k_hi,
                   const double* x_ri, const double* h_ri, double* chi_ri)
 {
@@ -78,15 +100,17 @@ void or_ambiguity(int M, int N, int L, const double* nu, int k_lo, int k_hi,
     cplx* chi = (cplx*)chi_ri;
     int D = k_hi - k_lo + 1;
     long long rows = (long long)M * M * D;
+    cplx* E = phasor_table(N, L, nu);
 #pragma omp parallel for schedule(dynamic, 4)
     for (long long r = 0; r < rows; ++r) {
         int d = (int)(r % D);
         int pair = (int)(r / D);
         int m = pair / M, l = pair % M;
         for (int j = 0; j < L; ++j)
-            chi[r * L + j] = af_cell(N, x + (size_t)m * N, h + (size_t)l * N,
-                                     k_lo + d, nu[j]);
+            chi[r * L + j] = af_cell_tab(N, x + (size_t)m * N, h + (size_t)l * N,
+                                         k_lo + d, E + (size_t)j * N);
     }
+    free(E);
 }
 
 /* Individual cells, for checking very large grids at sampled points. */
@@ -147,6 +171,7 @@ static void scan_af(const or_cfg* c, const cplx* x, const cplx* h, or_peak pk[2]
     int M = c->M, N = c->N, L = c->L, D = c->k_hi - c->k_lo + 1;
     long long rows = (long long)M * M * D;
     for (int cls = 0; cls < 2; ++cls) { pk[cls].vmax = 0; pk[cls].arg = -1; pk[cls].psum = 0; pk[cls].any = 0; }
+    cplx* E = phasor_table(N, L, c->nu);
     /* pass 1: max and argmax of w|chi| per class */
     double* rowmax = (double*)malloc(sizeof(double) * rows);
     long long* rowarg = (long long*)malloc(sizeof(long long) * rows);
@@ -159,7 +184,7 @@ static void scan_af(const or_cfg* c, const cplx* x, const cplx* h, or_peak pk[2]
         for (int j = 0; j < L; ++j) {
             double w = cell_weight(c, d, j);
             if (w <= 0) continue;
-            double v = w * cabs(af_cell(N, x + (size_t)m * N, h + (size_t)l * N, k, c->nu[j]));
+            double v = w * cabs(af_cell_tab(N, x + (size_t)m * N, h + (size_t)l * N, k, E + (size_t)j * N));
             if (v > rowmax[r]) { rowmax[r] = v; rowarg[r] = r * L + j; }
         }
     }
@@ -185,7 +210,7 @@ static void scan_af(const or_cfg* c, const cplx* x, const cplx* h, or_peak pk[2]
             for (int j = 0; j < L; ++j) {
                 double w = cell_weight(c, d, j);
                 if (w <= 0) continue;
-                double v = w * cabs(af_cell(N, x + (size_t)m * N, h + (size_t)l * N, k, c->nu[j]));
+                double v = w * cabs(af_cell_tab(N, x + (size_t)m * N, h + (size_t)l * N, k, E + (size_t)j * N));
                 s += pow(v / pk[cls].vmax, c->pnorm);
             }
             rowsum[r] = s;
@@ -197,7 +222,7 @@ static void scan_af(const or_cfg* c, const cplx* x, const cplx* h, or_peak pk[2]
         }
         free(rowsum);
     }
-    free(rowmax); free(rowarg);
+    free(rowmax); free(rowarg); free(E);
 }
 
 /* The class value that enters Eq. 37: the peak itself (exact max, the
@@ -567,17 +592,25 @@ void or_metrics(int M, int N, int L, const double* nu, int k_lo, int k_hi,
     int D = k_hi - k_lo + 1;
     double psl[2] = { 0, 0 };
     long long rows = (long long)M * M * D;
+    cplx* E = phasor_table(N, L, nu);
+    double* rowmax = (double*)calloc((size_t)rows, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 4)
     for (long long r = 0; r < rows; ++r) {
         int d = (int)(r % D), pair = (int)(r / D), m = pair / M, l = pair % M;
         int k = k_lo + d;
-        int cls = cell_class(m, l, k);
-        if (cls < 0) continue;
+        if (cell_class(m, l, k) < 0) continue;
         for (int j = 0; j < L; ++j) {
             if (w && !(w[(size_t)d * L + j] > 0)) continue;
-            double v = cabs(af_cell(N, x + (size_t)m * N, h + (size_t)l * N, k, nu[j]));
-            if (v > psl[cls]) psl[cls] = v;
+            double v = cabs(af_cell_tab(N, x + (size_t)m * N, h + (size_t)l * N, k, E + (size_t)j * N));
+            if (v > rowmax[r]) rowmax[r] = v;
         }
     }
+    for (long long r = 0; r < rows; ++r) {
+        int d = (int)(r % D), pair = (int)(r / D), m = pair / M, l = pair % M;
+        int cls = cell_class(m, l, k_lo + d);
+        if (cls >= 0 && rowmax[r] > psl[cls]) psl[cls] = rowmax[r];
+    }
+    free(rowmax); free(E);
     out[0] = 20.0 * log10(psl[0] / (double)N);
     out[1] = 20.0 * log10(psl[1] / (double)N);
     out[2] = out[0] > out[1] ? out[0] : out[1];
@@ -596,4 +629,43 @@ void or_metrics(int M, int N, int L, const double* nu, int k_lo, int k_hi,
     }
     out[3] = smax;
     (void)c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of Eq. 42 when the exact max is taken at a known cell, without   */
+/* scanning the grid (for grids too large to scan): the sidelobe term at     */
+/* that cell (weight w_cell) plus the SNRL term.  Same convention as         */
+/* or_grad_xh; chi_out receives chi at the cell.                             */
+/* ------------------------------------------------------------------------ */
+void or_grad_at_cell(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                     double w_cell, double eps, double snrl_db,
+                     const double* x_ri, const double* h_ri, long long cell,
+                     double* chi_out, double* gx_ri, double* gh_ri)
+{
+    or_cfg c = { M, N, L, k_lo, k_hi, nu, NULL, eps, snrl_db, 0.0 };
+    const cplx* x = (const cplx*)x_ri;
+    const cplx* h = (const cplx*)h_ri;
+    cplx* gx = (cplx*)gx_ri;
+    cplx* gh = (cplx*)gh_ri;
+    int D = k_hi - k_lo + 1;
+    memset(gx, 0, sizeof(cplx) * (size_t)M * N);
+    memset(gh, 0, sizeof(cplx) * (size_t)M * N);
+    int j = (int)(cell % L), d = (int)((cell / L) % D);
+    int pair = (int)(cell / ((long long)L * D));
+    cplx a = af_cell(N, x + (size_t)(pair / M) * N, h + (size_t)(pair % M) * N, k_lo + d, nu[j]);
+    if (chi_out) { chi_out[0] = creal(a); chi_out[1] = cimag(a); }
+    double mag = cabs(a);
+    if (mag > 0) add_cell_grad(&c, x, h, cell, eps * w_cell * a / mag, gx, gh);
+    double ptar = pow(10.0, -snrl_db / 20.0);
+    for (int m = 0; m < M; ++m) {
+        cplx a00 = 0;
+        for (int n = 0; n < N; ++n) a00 += x[(size_t)m * N + n] * conj(h[(size_t)m * N + n]);
+        double am = cabs(a00);
+        if (am <= 0) continue;
+        cplx G = (1.0 - eps) * (2.0 / M) * (am / N - ptar) / (double)N * a00 / am;
+        for (int n = 0; n < N; ++n) {
+            gx[(size_t)m * N + n] += G * h[(size_t)m * N + n];
+            gh[(size_t)m * N + n] += conj(G) * x[(size_t)m * N + n];
+        }
+    }
 }

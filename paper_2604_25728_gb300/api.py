@@ -1,0 +1,222 @@
+"""Python binding of the SQNGD C ABI (argument marshalling only).
+
+Every method forwards device pointers of torch tensors to the entry point of
+the same name in libsqngd.so; all arithmetic runs in the library's sm_103a
+kernels.  PyTorch provides device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import AF_PATH_AUTO, AF_PATH_DFT, AF_PATH_FFT, AF_PATH_SPLIT_BF16, AF_TERMS_FIXED, AfError  # noqa: F401
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, shape, name):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+class Context:
+    """One af_ctx: problem sizes, grid, loss and optimiser constants."""
+
+    def __init__(self, M, N, B, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, r_n=100,
+                 c=300.0, pnorm=0.0, path=AF_PATH_AUTO, n_h=10, n_x=10, lr_h=5e-2, lr_x=5e-4,
+                 beta1=0.9, beta2=0.999, adam_eps=1e-8, device=None, stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.M, self.N, self.B = int(M), int(N), int(B)
+        self.nu = np.ascontiguousarray(nu, dtype=np.float64)
+        self.L = int(self.nu.size)
+        self.k_lo, self.k_hi = int(k_lo), int(k_hi)
+        self.D = self.k_hi - self.k_lo + 1
+        self.r_n, self.c = int(r_n), float(c)
+        self.K = self.B * self.r_n
+        self.n_h, self.n_x = int(n_h), int(n_x)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        if w is not None and w.shape != (self.D, self.L):
+            raise ValueError(f"weights must be [D, L] = [{self.D}, {self.L}]")
+        cfg = _lib.AfConfig(
+            M=self.M, N=self.N, B=self.B, L=self.L,
+            nu=self.nu.ctypes.data_as(_lib.P_double), k_lo=self.k_lo, k_hi=self.k_hi,
+            weights=None if w is None else w.ctypes.data_as(_lib.P_float),
+            eps=float(eps), snrl_db=float(snrl_db), r_n=self.r_n, c=self.c, pnorm=float(pnorm),
+            path=int(path), n_h=self.n_h, n_x=self.n_x, lr_h=float(lr_h), lr_x=float(lr_x),
+            beta1=float(beta1), beta2=float(beta2), adam_eps=float(adam_eps))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            handle = ctypes.c_void_p()
+            st = self.lib.af_init(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle))
+            _lib.check(st, None)
+        self.handle = handle
+
+    # -------------------------------------------------------------- helpers
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.af_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        _lib.check(st, self.handle)
+
+    @property
+    def path(self) -> int:
+        return int(self.lib.af_path_of(self.handle))
+
+    def _mn(self, t, name, complex_=False):
+        _need(t, torch.complex64 if complex_ else torch.float32, (self.M, self.N), name)
+        return t
+
+    def empty_terms(self):
+        return torch.empty(AF_TERMS_FIXED + self.M, dtype=torch.float64, device=self.device)
+
+    # ------------------------------------------------------------ entry points
+    def af_sync(self):
+        self._check(self.lib.af_sync(self.handle))
+
+    def af_set_thresholds(self, rho):
+        r = np.ascontiguousarray(rho, dtype=np.float32)
+        if r.size != self.K:
+            raise ValueError(f"need K = {self.K} thresholds")
+        self._check(self.lib.af_set_thresholds(self.handle, r.ctypes.data_as(_lib.P_float)))
+
+    def af_ambiguity(self, x, h, chi=None):
+        self._mn(x, "x", True); self._mn(h, "h", True)
+        if chi is None:
+            chi = torch.empty((self.M, self.M, self.D, self.L), dtype=torch.complex64, device=self.device)
+        _need(chi, torch.complex64, (self.M, self.M, self.D, self.L), "chi")
+        self._check(self.lib.af_ambiguity(self.handle, _ptr(x), _ptr(h), _ptr(chi)))
+        return chi
+
+    def af_forward(self, x, h):
+        self._mn(x, "x", True); self._mn(h, "h", True)
+        self._check(self.lib.af_forward(self.handle, _ptr(x), _ptr(h)))
+
+    def af_loss_grad_xh(self, x, h, terms=None, grad_x=None, grad_h=None):
+        self._mn(x, "x", True); self._mn(h, "h", True)
+        terms = self.empty_terms() if terms is None else terms
+        self._check(self.lib.af_loss_grad_xh(self.handle, _ptr(x), _ptr(h), _ptr(terms), _ptr(grad_x), _ptr(grad_h)))
+        return terms, grad_x, grad_h
+
+    def af_loss_grad(self, u, h, use_hard=False, terms=None, grad_u=None, grad_h=None):
+        self._mn(u, "u"); self._mn(h, "h", True)
+        terms = self.empty_terms() if terms is None else terms
+        self._check(self.lib.af_loss_grad(self.handle, _ptr(u), _ptr(h), int(bool(use_hard)), _ptr(terms),
+                                          _ptr(grad_u), _ptr(grad_h)))
+        return terms, grad_u, grad_h
+
+    def quantize(self, z, q=None, x=None):
+        n = z.numel()
+        q = torch.empty(z.shape, dtype=torch.int32, device=self.device) if q is None else q
+        x = torch.empty(z.shape, dtype=torch.complex64, device=self.device) if x is None else x
+        self._check(self.lib.quantize(self.handle, _ptr(z), n, _ptr(q), _ptr(x)))
+        return q, x
+
+    def soft_quantize(self, z, y=None, dydz=None, x=None):
+        n = z.numel()
+        y = torch.empty_like(z) if y is None else y
+        dydz = torch.empty_like(z) if dydz is None else dydz
+        x = torch.empty(z.shape, dtype=torch.complex64, device=self.device) if x is None else x
+        self._check(self.lib.soft_quantize(self.handle, _ptr(z), n, _ptr(y), _ptr(dydz), _ptr(x)))
+        return y, dydz, x
+
+    def af_project(self, h):
+        self._mn(h, "h", True)
+        self._check(self.lib.af_project(self.handle, _ptr(h)))
+        return h
+
+    def sqngd_init(self, b, noise=None, u=None, h=None):
+        _need(b, torch.int32, (self.M, self.N), "b")
+        u = torch.empty((self.M, self.N), dtype=torch.float32, device=self.device) if u is None else u
+        h = torch.empty((self.M, self.N), dtype=torch.complex64, device=self.device) if h is None else h
+        self._check(self.lib.sqngd_init(self.handle, _ptr(b), _ptr(noise), _ptr(u), _ptr(h)))
+        return u, h
+
+    def sqngd_step(self, state: "SqngdState", n_outer: int, log: bool = True):
+        cs = state.c_struct()
+        buf = None
+        if log:
+            buf = np.zeros((n_outer, self.n_h + self.n_x, 4), dtype=np.float64)
+        self._check(self.lib.sqngd_step(self.handle, ctypes.byref(cs), int(n_outer),
+                                        None if buf is None else buf.ctypes.data_as(_lib.P_double)))
+        state.t_h, state.t_x, state.outer = cs.t_h, cs.t_x, cs.outer
+        return buf
+
+    def af_eval_hard(self, u, h):
+        self._mn(u, "u"); self._mn(h, "h", True)
+        out = np.zeros(4 + self.M, dtype=np.float64)
+        self._check(self.lib.af_eval_hard(self.handle, _ptr(u), _ptr(h), out.ctypes.data_as(_lib.P_double)))
+        return out
+
+
+@dataclass
+class SqngdState:
+    """Device buffers of the optimiser state (caller-owned, see af_state)."""
+    u: torch.Tensor
+    h: torch.Tensor
+    m_u: torch.Tensor
+    v_u: torch.Tensor
+    m_h: torch.Tensor
+    v_h: torch.Tensor
+    best_q: torch.Tensor
+    best_h: torch.Tensor
+    best: torch.Tensor
+    t_h: int = 0
+    t_x: int = 0
+    outer: int = 0
+
+    @classmethod
+    def create(cls, u, h):
+        z = torch.zeros_like
+        best = torch.tensor([float("inf"), float("inf"), -1.0, float("inf")], dtype=torch.float64,
+                            device=u.device)
+        return cls(u=u, h=h, m_u=z(u), v_u=z(u), m_h=z(h), v_h=z(h),
+                   best_q=torch.zeros(u.shape, dtype=torch.int32, device=u.device), best_h=h.clone(),
+                   best=best)
+
+    def c_struct(self):
+        return _lib.AfState(u_dev=self.u.data_ptr(), h_dev=self.h.data_ptr(), m_u_dev=self.m_u.data_ptr(),
+                            v_u_dev=self.v_u.data_ptr(), m_h_dev=self.m_h.data_ptr(), v_h_dev=self.v_h.data_ptr(),
+                            best_q_dev=self.best_q.data_ptr(), best_h_dev=self.best_h.data_ptr(),
+                            best_dev=self.best.data_ptr(), t_h=self.t_h, t_x=self.t_x, outer=self.outer)
+
+
+class AfLoss(torch.autograd.Function):
+    """Loss of Eq. 42 through the soft transmit chain; backward returns the
+    gradient the library's adjoint computed in the same call (scaled by the
+    incoming gradient)."""
+
+    @staticmethod
+    def forward(fctx, u, h, ctx: Context):
+        gu = torch.empty_like(u)
+        gh = torch.empty_like(h)
+        terms, _, _ = ctx.af_loss_grad(u.detach().contiguous(), h.detach().contiguous(), False,
+                                       grad_u=gu, grad_h=gh)
+        fctx.save_for_backward(gu, gh)
+        return terms[0].clone()
+
+    @staticmethod
+    def backward(fctx, g):
+        gu, gh = fctx.saved_tensors
+        s = g.to(torch.float32)
+        return gu * s, gh * s, None

@@ -1,0 +1,84 @@
+// af_kernels.h -- launch interfaces shared by the translation units of the
+// library (host side).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace af {
+
+// How a forward pass scores each cell.
+enum WeightMode : int {
+    WM_UNIFORM = 0,     // key = |chi|^2 (the uniform weight is applied afterwards)
+    WM_MAP = 1,         // key = w^2 |chi|^2, cells with w <= 0 skipped
+    WM_MAP_UNWEIGHTED = 2  // key = |chi|^2 on cells with w > 0 (acceptance PSL)
+};
+
+enum FwdMode : int {
+    FWD_REDUCE = 0,     // per-CTA max/argmax (+ p-norm partials), chi never stored
+    FWD_DUMP = 1        // write chi to chi_out [M][M][D][L]
+};
+
+// Arguments of the fused forward pass (product + Doppler transform +
+// sidelobe reduction).  C is float2 or double2, K the key type.
+template <typename C, typename K>
+struct FwdArgs {
+    int M, N, L, D, k_lo;
+    int n_chunks;          // delay chunks per pair; grid = M*M*n_chunks
+    int rows_per_chunk;    // multiple of the row slots per CTA
+    const C* x;            // [M][N] transmit waveforms (not Doppler-modulated)
+    const C* h;            // [M][N] receive filters
+    const C* pre;          // [N] e^{j 2 pi nu_0 n} (FFT grid) -- unused by the DFT path
+    const C* tw;           // FFT twiddle tables (FFT path) / [N][L] phasor table (DFT path)
+    const float* wmap;     // [D][L] ROI weights or nullptr
+    int weight_mode;       // WeightMode
+    int mode;              // FwdMode
+    float half_p;          // p/2 for the p-norm partials, 0 = exact max only
+    K* pkey;               // [grid] best key per CTA (-1 = none)
+    long long* pidx;       // [grid] its linear cell index
+    float* pvmax;          // [grid] p-norm partial: max key
+    float* psum;           // [grid] p-norm partial: sum (key/max)^(p/2)
+    double2* cdiag;        // [M] chi_mm(0,0) = sum_n x_m conj(h_m), FP64 (may be nullptr)
+    C* chi_out;            // FWD_DUMP output
+    long long* ctr_inc;    // if set, CTA 0 adds 1 to ctr_inc[0] (outer-iteration counter)
+};
+
+// FFT path: returns the dynamic shared memory bytes, or -1 if L unsupported.
+int fft_smem_bytes(int L, int N, bool fp64);
+int fft_rows_per_cta(int L);
+int fft_tw_len(int L);
+cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
+cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
+
+// Raise the dynamic shared-memory limit of the kernels a context will use
+// (FP32 forward: FFT or DFT; FP64 acceptance: FFT or DFT).
+cudaError_t fwd_prepare(bool fft, int L, int N);
+cudaError_t acc_prepare(bool fft, int L, int N);
+
+// Direct DFT path (any grid), SIMT.
+int dft_rows_per_cta();
+int dft_col_tiles(int L);
+cudaError_t launch_fwd_dft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
+cudaError_t launch_fwd_dft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
+
+struct QuantArgs;
+struct FinArgs;
+struct AccArgs;
+cudaError_t launch_wave_from_logits(const float* u, int n, const QuantArgs& q, int hard, float2* x,
+                                    float* dydz, int32_t* qout, cudaStream_t s);
+cudaError_t launch_quantize_z(const float* z, long long n, const QuantArgs& q, int32_t* qout, float2* x,
+                              cudaStream_t s);
+cudaError_t launch_soft_quantize_z(const float* z, long long n, const QuantArgs& q, float* y, float* dydz,
+                                   float2* x, cudaStream_t s);
+cudaError_t launch_wave_hard_f64(const float* u, const float2* h, int n, const QuantArgs& q,
+                                 const double2* level64, double2* x64, double2* h64, cudaStream_t s);
+cudaError_t launch_fin(const FinArgs& a, cudaStream_t s);
+cudaError_t launch_project(float2* h, int M, int N, cudaStream_t s);
+cudaError_t launch_init(const int32_t* b, const float2* noise, int n, int B, int r_n, const QuantArgs& q,
+                        float* u, float2* h, cudaStream_t s);
+cudaError_t launch_acceptance(const AccArgs& a, cudaStream_t s);
+cudaError_t launch_set_counters(long long* ctr, long long a0, long long a1, long long a2, long long a3,
+                                cudaStream_t s);
+cudaError_t launch_copy_f64(double* dst, const double* src, int n, cudaStream_t s);
+
+}  // namespace af

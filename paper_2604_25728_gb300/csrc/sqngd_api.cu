@@ -1,0 +1,673 @@
+// sqngd_api.cu -- the C ABI of include/sqngd.h: context, tables, workspace,
+// entry points and the CUDA-graph replay of Algorithm 1's outer iteration.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sqngd.h"
+#include "af_kernels.h"
+#include "af_step.cuh"
+
+using namespace af;
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// e^{j 2 pi t}, t in cycles, integer part removed first (FP64 on the host).
+inline void phasor(double t, double* re, double* im) {
+    const double f = t - floor(t);
+    *re = cos(kTwoPi * f);
+    *im = sin(kTwoPi * f);
+}
+
+struct FftPassInfo { int R, NS; };
+
+// Host mirror of the device FFT plan (radix 16 passes, then the remainder).
+std::vector<FftPassInfo> fft_plan(int L) {
+    std::vector<FftPassInfo> p;
+    int rem = L, ns = 1;
+    while (rem >= 16 && rem % 16 == 0) { p.push_back({16, ns}); ns *= 16; rem /= 16; }
+    if (rem > 1) p.push_back({rem, ns});
+    return p;
+}
+
+template <typename T> struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct af_ctx {
+    af_config cfg{};
+    std::vector<double> nu;
+    std::vector<float> wmap_host;
+    int D = 0, P = 0, K = 0, path = 0;
+    bool grid_fft = false;
+    double nu0 = 0.0;
+    float w0 = 0.f;
+    cudaStream_t stream = nullptr;     // caller's stream
+    cudaStream_t cap = nullptr;        // own stream for graph capture/replay
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int device = 0;
+    std::string err;
+
+    // tables
+    float2* pre = nullptr;     // [N] e^{j 2 pi nu0 n}
+    float2* tw = nullptr;      // FFT twiddles
+    float2* wL = nullptr;      // [L] e^{j 2 pi i / L}
+    float2* E = nullptr;       // [N][L] e^{j 2 pi nu_j n} (DFT path)
+    double2* pre64 = nullptr;
+    double2* tw64 = nullptr;
+    double2* E64 = nullptr;
+    float* wmap = nullptr;     // [D][L]
+    float* rho = nullptr;      // [K]
+    float2* level = nullptr;   // [B]
+    double2* level64 = nullptr;
+
+    // workspace
+    int n_chunks = 0, rows_per_chunk = 0, nblk = 0, ctas_per_pair = 0;
+    bool acc_fft = false;
+    int acc_n_chunks = 0, acc_rows_per_chunk = 0, acc_nblk = 0, acc_ctas_per_pair = 0;
+    float* pkey = nullptr;
+    long long* pidx = nullptr;
+    float* pvmax = nullptr;
+    float* psum = nullptr;
+    double* pkey64 = nullptr;
+    long long* pidx64 = nullptr;
+    double2* cdiag = nullptr;
+    float2* xs = nullptr;      // soft waveform
+    float* dydz = nullptr;
+    float2* xh = nullptr;      // hard waveform
+    double2* x64 = nullptr;
+    double2* h64 = nullptr;
+    double* acc_out = nullptr;
+    double* terms_scratch = nullptr;
+    int* errflag = nullptr;
+    long long* ctr = nullptr;  // [4]
+    double* best2 = nullptr;   // [8]
+    double* log = nullptr;
+    size_t log_cap_outer = 0;
+
+    // sqngd_step graph cache
+    cudaGraphExec_t gexec = nullptr;
+    af_state gkey{};
+    size_t g_log_cap = 0;
+};
+
+static std::string g_init_error;
+
+#define FAIL(ctx, code, ...)                                        \
+    do {                                                            \
+        char _b[512];                                               \
+        snprintf(_b, sizeof _b, __VA_ARGS__);                       \
+        (ctx)->err = _b;                                            \
+        return code;                                                \
+    } while (0)
+
+#define CK(ctx, call)                                                                      \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess) FAIL(ctx, AF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+    } while (0)
+
+template <typename T>
+static af_status dalloc(af_ctx* c, T** p, size_t n) {
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        FAIL(c, e == cudaErrorMemoryAllocation ? AF_ERR_OOM : AF_ERR_CUDA, "cudaMalloc(%zu bytes): %s",
+             n * sizeof(T), cudaGetErrorString(e));
+    }
+    return AF_OK;
+}
+
+template <typename T>
+static af_status upload(af_ctx* c, T** p, const std::vector<T>& v) {
+    af_status s = dalloc(c, p, v.size());
+    if (s != AF_OK) return s;
+    CK(c, cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return AF_OK;
+}
+
+static QuantArgs quant_args(const af_ctx* c) {
+    QuantArgs q{};
+    q.rho = c->rho;
+    q.K = c->K;
+    q.B = c->cfg.B;
+    q.a = (float)(1.0 / (2.0 * c->cfg.B));
+    q.c = (float)c->cfg.c;
+    q.win = (float)(12.0 / c->cfg.c);
+    q.level = c->level;
+    return q;
+}
+
+static void free_all(af_ctx* c) {
+    void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
+                    c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
+                    c->xs, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
+                    c->ctr, c->best2, c->log};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+}
+
+static af_status validate(const af_config* g, std::string* why) {
+    char b[256];
+    auto bad = [&](const char* m) { *why = m; return AF_ERR_INVALID_ARG; };
+    if (!g) return bad("cfg is NULL");
+    if (g->M < 1 || g->M > 16) return bad("M must be in 1..16");
+    if (g->N < 2 || g->N > 4096) return bad("N must be in 2..4096");
+    if (g->B < 2 || g->B > 1024) return bad("B must be in 2..1024");
+    if (g->L < 1 || g->L > 4096) return bad("L must be in 1..4096");
+    if (!g->nu) return bad("nu is NULL");
+    if (g->k_lo < -(g->N - 1) || g->k_hi > g->N - 1 || g->k_lo > g->k_hi) {
+        snprintf(b, sizeof b, "delay window [%d, %d] outside [-(N-1), N-1] or empty", g->k_lo, g->k_hi);
+        *why = b;
+        return AF_ERR_INVALID_ARG;
+    }
+    if (!(g->eps >= 0.0 && g->eps <= 1.0)) return bad("eps must be in [0, 1]");
+    if (!(g->snrl_db >= 0.0) || !isfinite(g->snrl_db)) return bad("snrl_db must be finite and >= 0");
+    if (g->r_n < 1 || (long long)g->B * g->r_n > (1 << 20)) return bad("r_n must be >= 1 with B*r_n <= 2^20");
+    if (!(g->c > 0.0) || !isfinite(g->c)) return bad("c must be finite and > 0");
+    if (!(g->pnorm >= 0.0) || (g->pnorm > 0.0 && g->pnorm < 1.0)) return bad("pnorm must be 0 or >= 1");
+    if (g->path < AF_PATH_AUTO || g->path > AF_PATH_SPLIT_BF16) return bad("unknown path");
+    if (g->n_h < 0 || g->n_x < 0 || g->n_h + g->n_x < 1 || g->n_h + g->n_x > 256)
+        return bad("n_h, n_x must be >= 0 with 1 <= n_h + n_x <= 256");
+    for (int j = 0; j < g->L; ++j)
+        if (!isfinite(g->nu[j])) return bad("nu has a non-finite value");
+    if (g->weights) {
+        const long long n = (long long)(g->k_hi - g->k_lo + 1) * g->L;
+        for (long long i = 0; i < n; ++i)
+            if (!(g->weights[i] >= 0.f) || !isfinite(g->weights[i])) return bad("weights must be finite and >= 0");
+    }
+    return AF_OK;
+}
+
+extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
+    if (!out) { g_init_error = "out is NULL"; return AF_ERR_INVALID_ARG; }
+    *out = nullptr;
+    std::string why;
+    if (validate(cfg, &why) != AF_OK) { g_init_error = why; return AF_ERR_INVALID_ARG; }
+    if (cfg->pnorm > 0.0) {
+        g_init_error = "pnorm > 0 needs the dense adjoint, which this build does not provide";
+        return AF_ERR_UNIMPLEMENTED;
+    }
+    if (cfg->path == AF_PATH_SPLIT_BF16) {
+        g_init_error = "AF_PATH_SPLIT_BF16 is not available in this build";
+        return AF_ERR_UNIMPLEMENTED;
+    }
+
+    af_ctx* c = new af_ctx();
+    c->cfg = *cfg;
+    c->cfg.nu = nullptr;
+    c->cfg.weights = nullptr;
+    if (c->cfg.beta1 == 0.0) c->cfg.beta1 = 0.9;
+    if (c->cfg.beta2 == 0.0) c->cfg.beta2 = 0.999;
+    if (c->cfg.adam_eps == 0.0) c->cfg.adam_eps = 1e-8;
+    const int M = cfg->M, N = cfg->N, L = cfg->L;
+    c->nu.assign(cfg->nu, cfg->nu + L);
+    c->D = cfg->k_hi - cfg->k_lo + 1;
+    c->P = M * M;
+    c->K = cfg->B * cfg->r_n;
+    c->w0 = (float)(1.0 / N);
+    c->stream = (cudaStream_t)stream;
+    auto fail = [&](af_status s) {
+        g_init_error = c->err;
+        free_all(c);
+        delete c;
+        return s;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) { c->err = "no CUDA device"; return fail(AF_ERR_CUDA); }
+
+    // ---- grid: uniform with spacing 1/L (FFT-able) or arbitrary ----
+    c->nu0 = c->nu[0];
+    bool uniform = (L >= 32 && L <= 4096 && (L & (L - 1)) == 0);
+    for (int j = 0; uniform && j < L; ++j)
+        if (fabs(c->nu[j] - (c->nu0 + (double)j / L)) > 1e-12) uniform = false;
+    const int fft_smem = uniform ? fft_smem_bytes(L, N, false) : -1;
+    uniform = uniform && fft_smem > 0 && fft_smem <= 227 * 1024;
+    if (cfg->path == AF_PATH_FFT && !uniform) {
+        c->err = "AF_PATH_FFT needs nu_j = nu_0 + j/L with L a power of two in 32..4096";
+        return fail(AF_ERR_UNIMPLEMENTED);
+    }
+    c->path = (cfg->path == AF_PATH_AUTO) ? (uniform ? AF_PATH_FFT : AF_PATH_DFT) : cfg->path;
+    c->grid_fft = uniform;
+
+    af_status s;
+    // ---- tables, built in FP64 ----
+    std::vector<float2> pre(N), wL(L), lev(c->cfg.B);
+    std::vector<double2> pre64(N), lev64(c->cfg.B);
+    for (int n = 0; n < N; ++n) {
+        double re, im;
+        phasor(c->nu0 * n, &re, &im);
+        pre[n] = make_float2((float)re, (float)im);
+        pre64[n] = make_double2(re, im);
+    }
+    for (int i = 0; i < L; ++i) {
+        double re, im;
+        phasor((double)i / L, &re, &im);
+        wL[i] = make_float2((float)re, (float)im);
+    }
+    for (int b = 0; b < c->cfg.B; ++b) {
+        double re, im;
+        phasor((double)b / c->cfg.B, &re, &im);
+        lev[b] = make_float2((float)re, (float)im);
+        lev64[b] = make_double2(re, im);
+    }
+    if ((s = upload(c, &c->pre, pre)) || (s = upload(c, &c->pre64, pre64)) || (s = upload(c, &c->wL, wL)) ||
+        (s = upload(c, &c->level, lev)) || (s = upload(c, &c->level64, lev64)))
+        return fail(s);
+    if (c->grid_fft) {
+        std::vector<float2> tw;
+        std::vector<double2> tw64;
+        const auto plan = fft_plan(L);
+        for (size_t p = 1; p < plan.size(); ++p) {
+            const int R = plan[p].R, NS = plan[p].NS;
+            for (int r = 0; r < R; ++r)
+                for (int k = 0; k < NS; ++k) {
+                    double re, im;
+                    phasor((double)r * k / ((double)NS * R), &re, &im);
+                    tw.push_back(make_float2((float)re, (float)im));
+                    tw64.push_back(make_double2(re, im));
+                }
+        }
+        if ((int)tw.size() != fft_tw_len(L)) { c->err = "internal: FFT twiddle table size mismatch"; return fail(AF_ERR_CUDA); }
+        if ((s = upload(c, &c->tw, tw)) || (s = upload(c, &c->tw64, tw64))) return fail(s);
+    }
+    {
+        // phasor table of the arbitrary-grid path (also used for acceptance when
+        // the FP64 FFT does not fit in shared memory)
+        std::vector<float2> E((size_t)N * L);
+        std::vector<double2> E64((size_t)N * L);
+        for (int n = 0; n < N; ++n)
+            for (int j = 0; j < L; ++j) {
+                double re, im;
+                phasor(c->nu[j] * n, &re, &im);
+                E[(size_t)n * L + j] = make_float2((float)re, (float)im);
+                E64[(size_t)n * L + j] = make_double2(re, im);
+            }
+        if ((s = upload(c, &c->E, E)) || (s = upload(c, &c->E64, E64))) return fail(s);
+    }
+    if (cfg->weights) {
+        c->wmap_host.assign(cfg->weights, cfg->weights + (size_t)c->D * L);
+        if ((s = upload(c, &c->wmap, c->wmap_host))) return fail(s);
+    }
+    {
+        std::vector<float> rho(c->K);
+        for (int i = 0; i < c->K; ++i) rho[i] = (float)(((double)i + 0.5) / (double)c->K);
+        if ((s = upload(c, &c->rho, rho))) return fail(s);
+    }
+
+    // kernels' shared-memory limits are raised here, outside any graph capture
+    {
+        cudaError_t e = fwd_prepare(c->path == AF_PATH_FFT, L, N);
+        if (e == cudaSuccess) e = acc_prepare(c->grid_fft && fft_smem_bytes(L, N, true) > 0 &&
+                                                  fft_smem_bytes(L, N, true) <= 227 * 1024, L, N);
+        if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
+    }
+
+    // ---- launch geometry and workspace ----
+    if (c->path == AF_PATH_FFT) {
+        const int RS = fft_rows_per_cta(L);
+        int it = (int)lround((double)c->P * c->D / ((double)RS * 152 * 6));
+        if (it < 1) it = 1;
+        if (const char* e = getenv("SQNGD_FFT_ROW_ITERS")) it = atoi(e) > 0 ? atoi(e) : it;
+        c->rows_per_chunk = RS * it;
+        c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
+        c->ctas_per_pair = c->n_chunks;
+    } else {
+        c->rows_per_chunk = dft_rows_per_cta();
+        c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
+        c->ctas_per_pair = c->n_chunks * dft_col_tiles(L);
+    }
+    c->nblk = c->P * c->ctas_per_pair;
+    // FP64 acceptance pass geometry
+    const int smem64 = c->grid_fft ? fft_smem_bytes(L, N, true) : -1;
+    c->acc_fft = c->grid_fft && smem64 > 0 && smem64 <= 227 * 1024;
+    if (c->acc_fft) {
+        const int RS = fft_rows_per_cta(L);
+        int it = (c->P * c->D) / (RS * 152 * 4);
+        if (it < 1) it = 1;
+        c->acc_rows_per_chunk = RS * it;
+        c->acc_n_chunks = (c->D + c->acc_rows_per_chunk - 1) / c->acc_rows_per_chunk;
+        c->acc_ctas_per_pair = c->acc_n_chunks;
+    } else {
+        c->acc_rows_per_chunk = dft_rows_per_cta();
+        c->acc_n_chunks = (c->D + c->acc_rows_per_chunk - 1) / c->acc_rows_per_chunk;
+        c->acc_ctas_per_pair = c->acc_n_chunks * dft_col_tiles(L);
+    }
+    c->acc_nblk = c->P * c->acc_ctas_per_pair;
+    const size_t MN = (size_t)M * N;
+    if ((s = dalloc(c, &c->pkey, c->nblk)) || (s = dalloc(c, &c->pidx, c->nblk)) ||
+        (s = dalloc(c, &c->pvmax, c->nblk)) || (s = dalloc(c, &c->psum, c->nblk)) ||
+        (s = dalloc(c, &c->pkey64, c->acc_nblk)) || (s = dalloc(c, &c->pidx64, c->acc_nblk)) ||
+        (s = dalloc(c, &c->cdiag, M)) || (s = dalloc(c, &c->xs, MN)) || (s = dalloc(c, &c->dydz, MN)) ||
+        (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
+        (s = dalloc(c, &c->acc_out, 4 + M)) || (s = dalloc(c, &c->terms_scratch, AF_TERMS_FIXED + M)) ||
+        (s = dalloc(c, &c->errflag, 1)) || (s = dalloc(c, &c->ctr, 4)) || (s = dalloc(c, &c->best2, 8)))
+        return fail(s);
+    if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) { c->err = "cudaMemset failed"; return fail(AF_ERR_CUDA); }
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        c->err = "stream/event creation failed";
+        return fail(AF_ERR_CUDA);
+    }
+    *out = c;
+    return AF_OK;
+}
+
+extern "C" af_status af_destroy(af_ctx* c) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->cap);
+    free_all(c);
+    delete c;
+    return AF_OK;
+}
+
+extern "C" const char* af_last_error(const af_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+extern "C" int32_t af_path_of(const af_ctx* c) { return c ? c->path : -1; }
+
+extern "C" af_status af_sync(af_ctx* c) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    CK(c, cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    CK(c, cudaMemcpy(&flag, c->errflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(c, cudaMemset(c->errflag, 0, sizeof(int)));
+        FAIL(c, AF_ERR_NONFINITE, "a loss or gradient was NaN or Inf");
+    }
+    return AF_OK;
+}
+
+extern "C" af_status af_set_thresholds(af_ctx* c, const float* rho_host) {
+    if (!c || !rho_host) return AF_ERR_INVALID_ARG;
+    for (int i = 0; i < c->K; ++i) {
+        if (!(rho_host[i] >= 0.f && rho_host[i] <= 1.f)) FAIL(c, AF_ERR_INVALID_ARG, "rho[%d] outside [0, 1]", i);
+        if (i > 0 && !(rho_host[i] > rho_host[i - 1])) FAIL(c, AF_ERR_INVALID_ARG, "rho not strictly increasing at %d", i);
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaMemcpy(c->rho, rho_host, sizeof(float) * c->K, cudaMemcpyHostToDevice));
+    return AF_OK;
+}
+
+// ---------------------------------------------------------------- forward --
+static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2* h) {
+    FwdArgs<float2, float> a{};
+    a.M = c->cfg.M; a.N = c->cfg.N; a.L = c->cfg.L; a.D = c->D; a.k_lo = c->cfg.k_lo;
+    a.n_chunks = c->n_chunks; a.rows_per_chunk = c->rows_per_chunk;
+    a.x = x; a.h = h; a.pre = c->pre;
+    a.tw = (c->path == AF_PATH_FFT) ? c->tw : c->E;
+    a.wmap = c->wmap;
+    a.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM;
+    a.mode = FWD_REDUCE;
+    a.half_p = (float)(c->cfg.pnorm * 0.5);
+    a.pkey = c->pkey; a.pidx = c->pidx; a.pvmax = c->pvmax; a.psum = c->psum;
+    a.cdiag = c->cdiag;
+    return a;
+}
+
+static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaStream_t s) {
+    return (c->path == AF_PATH_FFT) ? launch_fwd_fft_f32(a, s) : launch_fwd_dft_f32(a, s);
+}
+
+static FinArgs fin_args(af_ctx* c) {
+    FinArgs f{};
+    f.M = c->cfg.M; f.N = c->cfg.N; f.L = c->cfg.L; f.D = c->D; f.k_lo = c->cfg.k_lo;
+    f.nblk = c->nblk; f.ctas_per_pair = c->ctas_per_pair;
+    f.pkey = c->pkey; f.pidx = c->pidx; f.pvmax = c->pvmax; f.psum = c->psum;
+    f.cdiag = c->cdiag;
+    f.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM;
+    f.w0 = c->w0; f.wmap = c->wmap;
+    f.eps = c->cfg.eps;
+    f.ptar = pow(10.0, -c->cfg.snrl_db / 20.0);
+    f.half_p = (float)(c->cfg.pnorm * 0.5);
+    f.grid_fft = c->grid_fft ? 1 : 0;
+    f.pre = c->pre; f.wL = c->wL; f.E = c->E;
+    f.err_flag = c->errflag;
+    f.qa = quant_args(c);
+    f.snrl_db = c->cfg.snrl_db;
+    f.n_h = c->cfg.n_h; f.n_x = c->cfg.n_x;
+    f.evals_per_outer = c->cfg.n_h + c->cfg.n_x;
+    f.lr = 0.f;
+    f.b1 = (float)c->cfg.beta1; f.b2 = (float)c->cfg.beta2; f.adam_eps = (float)c->cfg.adam_eps;
+    return f;
+}
+
+extern "C" af_status af_ambiguity(af_ctx* c, const float* x, const float* h, float* chi) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!x || !h || !chi) FAIL(c, AF_ERR_INVALID_ARG, "af_ambiguity: NULL pointer");
+    FwdArgs<float2, float> a = fwd_args(c, (const float2*)x, (const float2*)h);
+    a.mode = FWD_DUMP;
+    a.chi_out = (float2*)chi;
+    a.cdiag = nullptr;
+    CK(c, launch_fwd(c, a, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status af_forward(af_ctx* c, const float* x, const float* h) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!x || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_forward: x and h must not be NULL");
+    CK(c, launch_fwd(c, fwd_args(c, (const float2*)x, (const float2*)h), c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status af_loss_grad_xh(af_ctx* c, const float* x, const float* h, double* terms, float* gx,
+                                     float* gh) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!x || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_xh: x and h must not be NULL");
+    CK(c, launch_fwd(c, fwd_args(c, (const float2*)x, (const float2*)h), c->stream));
+    FinArgs f = fin_args(c);
+    f.mode = FIN_GRAD_XH;
+    f.x = (const float2*)x;
+    f.h_in = (const float2*)h;
+    f.terms = terms;
+    f.grad_x = (float2*)gx;
+    f.grad_h = (float2*)gh;
+    CK(c, launch_fin(f, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status af_loss_grad(af_ctx* c, const float* u, const float* h, int32_t use_hard, double* terms,
+                                  float* gu, float* gh) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!u || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad: u and h must not be NULL");
+    const int MN = c->cfg.M * c->cfg.N;
+    QuantArgs q = quant_args(c);
+    float2* x = use_hard ? c->xh : c->xs;
+    CK(c, launch_wave_from_logits(u, MN, q, use_hard ? 1 : 0, x, c->dydz, nullptr, c->stream));
+    CK(c, launch_fwd(c, fwd_args(c, x, (const float2*)h), c->stream));
+    FinArgs f = fin_args(c);
+    f.mode = use_hard ? FIN_GRAD_XH : FIN_GRAD_U;
+    f.x = x;
+    f.dydz = c->dydz;
+    f.u = const_cast<float*>(u);
+    f.h_in = (const float2*)h;
+    f.terms = terms;
+    f.grad_u = use_hard ? nullptr : gu;
+    f.grad_h = (float2*)gh;
+    CK(c, launch_fin(f, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status quantize(af_ctx* c, const float* z, int64_t n, int32_t* q, float* x) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !z)) FAIL(c, AF_ERR_INVALID_ARG, "quantize: bad z/n");
+    QuantArgs qa = quant_args(c);
+    CK(c, launch_quantize_z(z, n, qa, q, (float2*)x, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status soft_quantize(af_ctx* c, const float* z, int64_t n, float* y, float* dydz, float* x) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && !z)) FAIL(c, AF_ERR_INVALID_ARG, "soft_quantize: bad z/n");
+    QuantArgs qa = quant_args(c);
+    CK(c, launch_soft_quantize_z(z, n, qa, y, dydz, (float2*)x, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status af_project(af_ctx* c, float* h) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!h) FAIL(c, AF_ERR_INVALID_ARG, "af_project: h is NULL");
+    CK(c, launch_project((float2*)h, c->cfg.M, c->cfg.N, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status sqngd_init(af_ctx* c, const int32_t* b, const float* noise, float* u, float* h) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!b || !u || !h) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_init: b, u and h must not be NULL");
+    const int MN = c->cfg.M * c->cfg.N;
+    CK(c, launch_init(b, (const float2*)noise, MN, c->cfg.B, c->cfg.r_n, quant_args(c), u, (float2*)h, c->stream));
+    CK(c, launch_project((float2*)h, c->cfg.M, c->cfg.N, c->stream));
+    return AF_OK;
+}
+
+// ------------------------------------------------------------- sqngd_step --
+static bool same_state(const af_state& a, const af_state& b) {
+    return a.u_dev == b.u_dev && a.h_dev == b.h_dev && a.m_u_dev == b.m_u_dev && a.v_u_dev == b.v_u_dev &&
+           a.m_h_dev == b.m_h_dev && a.v_h_dev == b.v_h_dev && a.best_q_dev == b.best_q_dev &&
+           a.best_h_dev == b.best_h_dev;
+}
+
+// Enqueue one outer iteration of Algorithm 1 (used for capture).
+static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
+    const int nh = c->cfg.n_h, nx = c->cfg.n_x;
+    const int MN = c->cfg.M * c->cfg.N;
+    float2* h = (float2*)st->h_dev;
+    bool first = true;
+    if (nh == 0) CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 0, c->xs, c->dydz, nullptr, s));
+    for (int i = 0; i < nh; ++i) {
+        FwdArgs<float2, float> a = fwd_args(c, c->xh, h);
+        if (first) { a.ctr_inc = c->ctr; first = false; }
+        CK(c, launch_fwd(c, a, s));
+        FinArgs f = fin_args(c);
+        f.mode = FIN_ADAM_H;
+        f.x = c->xh; f.h_in = h; f.h = h;
+        f.m_h = (float2*)st->m_h_dev; f.v_h = (float2*)st->v_h_dev;
+        f.u = st->u_dev;
+        f.lr = (float)c->cfg.lr_h;
+        f.ctr = c->ctr; f.inner = i;
+        f.log = c->log; f.eval_index = i;
+        f.snap_best = (i == 0) ? 1 : 0;
+        f.best2 = c->best2; f.best_q = st->best_q_dev; f.best_h = (float2*)st->best_h_dev;
+        f.next_wave = (i == nh - 1) ? NEXT_SOFT : NEXT_NONE;
+        f.x_next = c->xs; f.dydz_next = c->dydz;
+        CK(c, launch_fin(f, s));
+    }
+    for (int j = 0; j < nx; ++j) {
+        FwdArgs<float2, float> a = fwd_args(c, c->xs, h);
+        if (first) { a.ctr_inc = c->ctr; first = false; }
+        CK(c, launch_fwd(c, a, s));
+        FinArgs f = fin_args(c);
+        f.mode = FIN_ADAM_U;
+        f.x = c->xs; f.dydz = c->dydz; f.h_in = h;
+        f.u = st->u_dev; f.m_u = st->m_u_dev; f.v_u = st->v_u_dev;
+        f.lr = (float)c->cfg.lr_x;
+        f.ctr = c->ctr; f.inner = j;
+        f.log = c->log; f.eval_index = nh + j;
+        f.next_wave = (j == nx - 1) ? NEXT_HARD : NEXT_SOFT;
+        f.x_next = (j == nx - 1) ? c->xh : c->xs;
+        f.dydz_next = c->dydz;
+        CK(c, launch_fin(f, s));
+    }
+    return AF_OK;
+}
+
+extern "C" af_status sqngd_step(af_ctx* c, af_state* st, int32_t n_outer, double* log_host) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!st || !st->u_dev || !st->h_dev || !st->m_u_dev || !st->v_u_dev || !st->m_h_dev || !st->v_h_dev)
+        FAIL(c, AF_ERR_INVALID_ARG, "sqngd_step: state buffers must not be NULL");
+    if (n_outer < 0) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_step: n_outer < 0");
+    if (n_outer == 0) return AF_OK;
+    const int ev = c->cfg.n_h + c->cfg.n_x;
+    const int MN = c->cfg.M * c->cfg.N;
+
+    // log capacity (the captured graph indexes the log by the device counter)
+    if ((size_t)n_outer > c->log_cap_outer) {
+        CK(c, cudaStreamSynchronize(c->cap));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (c->log) cudaFree(c->log);
+        c->log = nullptr;
+        size_t cap = 64;
+        while (cap < (size_t)n_outer) cap *= 2;
+        af_status s = dalloc(c, &c->log, cap * ev * 4);
+        if (s != AF_OK) return s;
+        c->log_cap_outer = cap;
+        if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    }
+    if (c->gexec && !same_state(c->gkey, *st)) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (!c->gexec) {
+        cudaGraph_t g = nullptr;
+        CK(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        af_status s = enqueue_outer(c, st, c->cap);
+        cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        if (s != AF_OK) { if (g) cudaGraphDestroy(g); return s; }
+        if (e != cudaSuccess) FAIL(c, AF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { c->gexec = nullptr; FAIL(c, AF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        c->gkey = *st;
+    }
+
+    CK(c, cudaEventRecord(c->ev_in, c->stream));
+    CK(c, cudaStreamWaitEvent(c->cap, c->ev_in, 0));
+    CK(c, launch_set_counters(c->ctr, 0, st->t_h, st->t_x, st->outer, c->cap));
+    if (st->best_dev) CK(c, launch_copy_f64(c->best2 + 4, st->best_dev, 4, c->cap));
+    else {
+        const double init[4] = {INFINITY, INFINITY, -1.0, INFINITY};
+        CK(c, cudaMemcpyAsync(c->best2 + 4, init, sizeof init, cudaMemcpyHostToDevice, c->cap));
+    }
+    CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 1, c->xh, nullptr, nullptr, c->cap));
+    for (int o = 0; o < n_outer; ++o) CK(c, cudaGraphLaunch(c->gexec, c->cap));
+    if (st->best_dev && c->cfg.n_h > 0)
+        CK(c, launch_copy_f64(st->best_dev, c->best2 + ((n_outer - 1) & 1) * 4, 4, c->cap));
+    if (log_host)
+        CK(c, cudaMemcpyAsync(log_host, c->log, sizeof(double) * (size_t)n_outer * ev * 4, cudaMemcpyDeviceToHost, c->cap));
+    CK(c, cudaEventRecord(c->ev_out, c->cap));
+    CK(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+    st->t_h += (int64_t)n_outer * c->cfg.n_h;
+    st->t_x += (int64_t)n_outer * c->cfg.n_x;
+    st->outer += n_outer;
+    if (log_host) return af_sync(c);
+    return AF_OK;
+}
+
+// ------------------------------------------------------------- acceptance --
+extern "C" af_status af_eval_hard(af_ctx* c, const float* u, const float* h, double* out_host) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!u || !h || !out_host) FAIL(c, AF_ERR_INVALID_ARG, "af_eval_hard: NULL pointer");
+    const int M = c->cfg.M, N = c->cfg.N, MN = M * N;
+    CK(c, launch_wave_hard_f64(u, (const float2*)h, MN, quant_args(c), c->level64, c->x64, c->h64, c->stream));
+    FwdArgs<double2, double> a{};
+    a.M = M; a.N = N; a.L = c->cfg.L; a.D = c->D; a.k_lo = c->cfg.k_lo;
+    a.n_chunks = c->acc_n_chunks; a.rows_per_chunk = c->acc_rows_per_chunk;
+    a.x = c->x64; a.h = c->h64; a.pre = c->pre64;
+    a.tw = c->acc_fft ? c->tw64 : c->E64;
+    a.wmap = c->wmap;
+    a.weight_mode = c->wmap ? WM_MAP_UNWEIGHTED : WM_UNIFORM;
+    a.mode = FWD_REDUCE;
+    a.half_p = 0.f;
+    a.pkey = c->pkey64; a.pidx = c->pidx64;
+    a.cdiag = c->cdiag;
+    CK(c, c->acc_fft ? launch_fwd_fft_f64(a, c->stream) : launch_fwd_dft_f64(a, c->stream));
+    AccArgs g{};
+    g.M = M; g.N = N; g.nblk = c->acc_nblk; g.ctas_per_pair = c->acc_ctas_per_pair;
+    g.pkey = c->pkey64; g.cdiag = c->cdiag; g.x = c->x64; g.h = c->h64; g.out = c->acc_out;
+    CK(c, launch_acceptance(g, c->stream));
+    CK(c, cudaMemcpyAsync(out_host, c->acc_out, sizeof(double) * (4 + M), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return AF_OK;
+}

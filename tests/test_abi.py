@@ -1,0 +1,106 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every entry point include/sqngd.h declares, its ctypes structs match the C
+layout, and host-side validation rejects bad configurations before any CUDA
+call."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sqngd.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^AF_API\s+[\w\s\*]+?\b(\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_25728_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("af_init", "af_destroy", "af_loss_grad", "af_loss_grad_xh", "af_ambiguity", "quantize",
+              "soft_quantize", "af_project", "sqngd_init", "sqngd_step", "af_eval_hard", "af_sync",
+              "af_last_error", "af_set_thresholds", "af_path_of"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2604_25728_gb300 import _lib
+    names = _declared()
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.lib_path()], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+        assert n in _lib.SIGNATURES, n
+    # nothing else leaks out of the library
+    assert exported == set(names)
+
+
+def test_ctypes_structs_match_c_layout(tmp_path):
+    from paper_2604_25728_gb300 import _lib
+    src = tmp_path / "layout.c"
+    fields_c = [f for f, _ in _lib.AfConfig._fields_]
+    fields_s = [f for f, _ in _lib.AfState._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sqngd.h"', 'int main(void){']
+    lines.append('printf("af_config %zu\\n", sizeof(af_config));')
+    lines.append('printf("af_state %zu\\n", sizeof(af_state));')
+    for f in fields_c:
+        lines.append(f'printf("af_config.{f} %zu\\n", offsetof(af_config, {f}));')
+    for f in fields_s:
+        lines.append(f'printf("af_state.{f} %zu\\n", offsetof(af_state, {f}));')
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    assert int(got["af_config"]) == ctypes.sizeof(_lib.AfConfig)
+    assert int(got["af_state"]) == ctypes.sizeof(_lib.AfState)
+    for f in fields_c:
+        assert int(got[f"af_config.{f}"]) == getattr(_lib.AfConfig, f).offset, f
+    for f in fields_s:
+        assert int(got[f"af_state.{f}"]) == getattr(_lib.AfState, f).offset, f
+
+
+def _cfg(**kw):
+    from paper_2604_25728_gb300 import _lib
+    nu = np.array(kw.pop("nu", [-0.5 + j / 32 for j in range(32)]), dtype=np.float64)
+    base = dict(M=2, N=32, B=4, L=nu.size, k_lo=-31, k_hi=31, eps=0.1, snrl_db=0.5, r_n=3, c=300.0,
+                pnorm=0.0, path=0, n_h=1, n_x=1, lr_h=0.05, lr_x=1e-3, beta1=0.9, beta2=0.999, adam_eps=1e-8)
+    base.update(kw)
+    cfg = _lib.AfConfig(**base)
+    cfg.nu = nu.ctypes.data_as(_lib.P_double)
+    return cfg, nu
+
+
+@pytest.mark.parametrize("bad", [dict(M=0), dict(M=17), dict(N=1), dict(N=5000), dict(B=1), dict(k_lo=-40),
+                                 dict(k_lo=3, k_hi=2), dict(eps=1.5), dict(snrl_db=-1.0), dict(r_n=0),
+                                 dict(c=0.0), dict(pnorm=0.5), dict(path=9), dict(n_h=0, n_x=0),
+                                 dict(L=0), dict(nu=[0.0, float("nan")])])
+def test_init_rejects_bad_config_on_host(lib, bad):
+    from paper_2604_25728_gb300 import _lib
+    cfg, nu = _cfg(**bad)
+    h = ctypes.c_void_p()
+    st = lib.af_init(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert st == _lib.AF_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.af_last_error(None).decode() != ""
+
+
+def test_null_arguments_are_rejected(lib):
+    from paper_2604_25728_gb300 import _lib
+    assert lib.af_init(None, None, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.af_destroy(None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.af_sync(None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.af_loss_grad(None, None, None, 0, None, None, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.sqngd_step(None, None, 1, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.af_path_of(None) == -1

@@ -388,3 +388,19 @@ def test_outer_iteration_structure(orc):
     orc.sqngd_outer(st, cfg)
     np.testing.assert_array_equal(st["h"], h_after)
     assert st["t_x"] == 2 and not np.array_equal(st["u"], u)
+
+
+def test_grad_at_cell_equals_full_gradient_at_that_cell(orc):
+    """The no-scan gradient equals the full-scan gradient differentiated at the
+    same cell (the argmax, and a non-argmax cell passed explicitly)."""
+    M, N = 2, 14
+    x, h = _random_pair(17, M, N)
+    nu = wl.full_grid(8)
+    r = orc.loss(x, h, nu, -(N - 1), N - 1, eps=0.3, snrl_db=0.4)
+    for cell in (r["cells"][r["cls"]], 37):
+        _, gx, gh = orc.grad_xh(x, h, nu, -(N - 1), N - 1, eps=0.3, snrl_db=0.4, use_cell=cell)
+        chi, gx2, gh2 = orc.grad_at_cell(x, h, nu, -(N - 1), N - 1, cell, 1.0 / N, eps=0.3, snrl_db=0.4)
+        np.testing.assert_allclose(gx2, gx, atol=1e-14)
+        np.testing.assert_allclose(gh2, gh, atol=1e-14)
+        full = orc.ambiguity(x, h, nu, -(N - 1), N - 1).reshape(-1)
+        assert abs(chi - full[cell]) < 1e-12
