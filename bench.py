@@ -41,6 +41,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--fwd-only", type=int, default=0,
+                   help="run only N launches of the fused forward pass on the workload (for profiler captures)")
     return p.parse_args()
 
 
@@ -245,6 +247,14 @@ def run_ours(args):
     b = torch.from_numpy(wl.phase_indices(seed, w.M, w.N, w.B)).to(dev)
     u, h = ctx.sqngd_init(b)
     st = api.SqngdState.create(u, h)
+    if args.fwd_only > 0:
+        xh = torch.empty((w.M, w.N), dtype=torch.complex64, device=dev)
+        ctx.quantize(torch.sigmoid(st.u), x=xh)
+        for _ in range(args.fwd_only):
+            ctx.af_forward(xh, st.h)
+        ctx.af_sync()
+        ctx.close()
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     evals_per_step = w.n_h + w.n_x
 

@@ -87,62 +87,89 @@ template <int ST> struct Dft<1, ST> {
 };
 
 // ----------------------------------------------------------- FFT plan ------
-// L = 16^a * r with r in {1, 2, 4, 8}; E = 16 values per thread, T = L/16
-// threads per row; pass p has radix R(p) and NS(p) = product of the previous
-// radices.  Stockham auto-sort: the output of the last pass is in natural
-// order, thread t holding bins b + r*NS_last for b = t + T*s.
-template <int L> struct Plan {
-    static_assert(L >= 32 && L <= 4096 && (L & (L - 1)) == 0, "L must be a power of two in [32, 4096]");
-    static constexpr int E = 16;
-    static constexpr int T = L / 16;
-    static constexpr int n16 = (L >= 4096) ? 3 : (L >= 256) ? 2 : 1;
-    static constexpr int rem = L / (n16 == 3 ? 4096 : n16 == 2 ? 256 : 16);  // 1, 2, 4 or 8
-    static constexpr int passes = n16 + (rem > 1 ? 1 : 0);
-    static constexpr int radix(int p) { return p < n16 ? 16 : rem; }
+// L = E^a * r (E = 8 or 16 values per thread, r a smaller power of two), so
+// T = L/E threads own one row.  Pass p has radix R(p) (E, then the
+// remainder) and NS(p) = product of the previous radices.  Stockham
+// auto-sort: after the last pass thread t holds bins b + r*NS_last for
+// b = t + T*s, in natural order.
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+template <int L, int E> struct Plan {
+    static_assert(E == 8 || E == 16, "E must be 8 or 16");
+    static_assert(L >= 2 * E && L <= 4096 && (L & (L - 1)) == 0, "L must be a power of two in [2E, 4096]");
+    static constexpr int T = L / E;
+    static constexpr int lgE = ilog2c(E);
+    static constexpr int nfull = ilog2c(L) / lgE;
+    static constexpr int rem = 1 << (ilog2c(L) - nfull * lgE);
+    static constexpr int passes = nfull + (rem > 1 ? 1 : 0);
+    static constexpr int radix(int p) { return p < nfull ? E : rem; }
     static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
     // offset of pass p's twiddle table [R][NS] (pass 0 has none)
     static constexpr int tw_off(int p) { return p <= 1 ? 0 : tw_off(p - 1) + radix(p - 1) * ns(p - 1); }
     static constexpr int tw_len = tw_off(passes - 1) + radix(passes - 1) * ns(passes - 1);
-    static constexpr int padlen = L + L / 16;      // row buffer length with one pad per 16
+    static constexpr int padlen = L + L / E;       // row buffer with one pad slot per E
 };
 
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+// Padded buffer index: one unused slot after every E entries, which makes
+// the strided exchanges below free of shared-memory bank conflicts.
+template <int E> __device__ __forceinline__ int padE(int i) { return i + (i >> ilog2c(E)); }
 
 // Twiddle multiply + radix-R butterflies of pass (R, NS) on registers.
-template <int L, int R, int NS, typename C>
-__device__ __forceinline__ void pass_compute(C (&v)[16], int t, const C* tw) {
-    constexpr int T = L / 16, NB = 16 / R;
+template <int L, int E, int R, int NS, typename C>
+__device__ __forceinline__ void pass_compute(C (&v)[E], int t, const C* tw) {
+    constexpr int T = L / E, NB = E / R;
 #pragma unroll
     for (int s = 0; s < NB; ++s) {
         if constexpr (NS > 1) {
-            const int k = (t + T * s) & (NS - 1);
+            const C* tk = tw + ((t + T * s) & (NS - 1));
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[s * R + r] = cmul(v[s * R + r], tw[r * NS + k]);
+            for (int r = 1; r < R; ++r) v[s * R + r] = cmul(v[s * R + r], tk[r * NS]);
         }
         Dft<R, 1>::run(&v[s * R]);
     }
 }
 
-template <int L, int R, int NS, typename C>
-__device__ __forceinline__ void pass_store(const C (&v)[16], int t, C* buf) {
-    constexpr int T = L / 16, NB = 16 / R;
+// Stockham write of a pass's outputs: value r of butterfly b goes to
+// (b/NS) NS R + (b mod NS) + r NS.  Pass 0 (NS = 1) has R = E and every later
+// pass has NS a multiple of E, so the padded address is a per-butterfly base
+// plus a compile-time offset.
+template <int L, int E, int R, int NS, typename C>
+__device__ __forceinline__ void pass_store(const C (&v)[E], int t, C* buf) {
+    constexpr int T = L / E, NB = E / R;
+    static_assert(NS == 1 || NS % E == 0, "pass layout");
 #pragma unroll
     for (int s = 0; s < NB; ++s) {
         const int b = t + T * s;
-        const int base = (b / NS) * NS * R + (b & (NS - 1));
+        C* p;
+        if constexpr (NS == 1) {
+            static_assert(R == E, "pass 0 has radix E");
+            p = buf + b * (E + 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad16(base + r * NS)] = v[s * R + r];
+            for (int r = 0; r < R; ++r) p[r] = v[s * R + r];
+        } else {
+            const int base = (b / NS) * NS * R + (b & (NS - 1));
+            p = buf + padE<E>(base);
+#pragma unroll
+            for (int r = 0; r < R; ++r) p[r * (NS / E) * (E + 1)] = v[s * R + r];
+        }
     }
 }
 
-template <int L, int R, typename C>
-__device__ __forceinline__ void pass_load(C (&v)[16], int t, const C* buf) {
-    constexpr int T = L / 16, NB = 16 / R;
+// Stockham read of a pass's inputs: value r of butterfly b is at b + r L/R.
+template <int L, int E, int R, typename C>
+__device__ __forceinline__ void pass_load(C (&v)[E], int t, const C* buf) {
+    constexpr int T = L / E, NB = E / R, ST = L / R;
+    if constexpr (ST % E == 0 && T % E == 0) {
+        const C* p = buf + padE<E>(t);
 #pragma unroll
-    for (int s = 0; s < NB; ++s) {
-        const int b = t + T * s;
+        for (int s = 0; s < NB; ++s)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[s * R + r] = buf[pad16(b + r * (L / R))];
+            for (int r = 0; r < R; ++r) v[s * R + r] = p[(T * s + r * ST) / E * (E + 1)];
+    } else {
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[s * R + r] = buf[padE<E>(t + T * s + r * ST)];
     }
 }
 
@@ -157,28 +184,19 @@ __device__ __forceinline__ void row_sync(int slot) {
 }
 
 // Passes 1..P-1 (pass 0 has been computed into v by the caller).
-template <int L, int P, typename C>
-__device__ __forceinline__ void fft_rest(C (&v)[16], int t, int slot, C* buf, const C* tw) {
-    using PL = Plan<L>;
+template <int L, int E, int P, typename C>
+__device__ __forceinline__ void fft_rest(C (&v)[E], int t, int slot, C* buf, const C* tw) {
+    using PL = Plan<L, E>;
     if constexpr (P < PL::passes) {
         constexpr int Rp = PL::radix(P - 1), NSp = PL::ns(P - 1);
         constexpr int R = PL::radix(P), NS = PL::ns(P);
-        pass_store<L, Rp, NSp>(v, t, buf);
+        pass_store<L, E, Rp, NSp>(v, t, buf);
         row_sync<PL::T>(slot);
-        pass_load<L, R>(v, t, buf);
+        pass_load<L, E, R>(v, t, buf);
         row_sync<PL::T>(slot);
-        pass_compute<L, R, NS>(v, t, tw + PL::tw_off(P));
-        fft_rest<L, P + 1>(v, t, slot, buf, tw);
+        pass_compute<L, E, R, NS>(v, t, tw + PL::tw_off(P));
+        fft_rest<L, E, P + 1>(v, t, slot, buf, tw);
     }
-}
-
-// Bin index held in v[s*R + r] after the last pass.
-template <int L>
-__device__ __forceinline__ int out_bin(int t, int s, int r) {
-    using PL = Plan<L>;
-    constexpr int R = PL::radix(PL::passes - 1), NS = PL::ns(PL::passes - 1);
-    return t + PL::T * s + r * NS;
-    (void)R;
 }
 
 }  // namespace af

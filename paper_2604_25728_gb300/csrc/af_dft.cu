@@ -219,15 +219,8 @@ static cudaError_t prepare_dft(int N) {
     return set_smem_once(reinterpret_cast<const void*>(fwd_dft_kernel<C, K>), smem);
 }
 
-cudaError_t fft_prepare_f32(int L, int N);
-cudaError_t fft_prepare_f64(int L, int N);
-
-cudaError_t fwd_prepare(bool fft, int L, int N) {
-    return fft ? fft_prepare_f32(L, N) : prepare_dft<float2, float>(N);
-}
-cudaError_t acc_prepare(bool fft, int L, int N) {
-    return fft ? fft_prepare_f64(L, N) : prepare_dft<double2, double>(N);
-}
+cudaError_t dft_prepare_f32(int N) { return prepare_dft<float2, float>(N); }
+cudaError_t dft_prepare_f64(int N) { return prepare_dft<double2, double>(N); }
 
 int dft_rows_per_cta() { return TR; }
 int dft_col_tiles(int L) { return (L + TC - 1) / TC; }

@@ -4,17 +4,21 @@
 //   chi_ml(k, nu_j) = sum_n x_m(n) conj(h_l(n+k)) e^{j 2 pi nu_0 n} e^{+j 2 pi j n / L}
 // i.e. an unnormalised inverse-sign L-point DFT of the lag products
 // (folded modulo L when N > L, zero-padded when N < L).  One CTA owns one
-// pair and a chunk of delays; x_m (pre-modulated by e^{j 2 pi nu_0 n}) and h_l
-// sit in shared memory, each row's products are formed in registers and
-// transformed by a Stockham FFT (radix 16/16/r, 16 values per thread, T = L/16
-// threads per row, exchanges through a padded shared buffer).  The last pass
-// leaves chi in registers, where the sidelobe reduction of Eqs. 7-9 runs:
-// per-CTA max of w^2|chi|^2 with its lowest linear cell index, plus p-norm
-// partials.  chi is never written to memory in the reduce mode.
+// pair and a chunk of delays.  x_m (pre-modulated by e^{j 2 pi nu_0 n}, zero
+// beyond N) and h_l (with N zeros on each side) sit in shared memory, so each
+// row's products are formed in registers without bounds checks.  The row is
+// transformed by a Stockham FFT with E values per thread (T = L/E threads per
+// row, radix E passes then the remainder, exchanges through a padded shared
+// buffer).  The last pass leaves chi in registers, where the sidelobe
+// reduction of Eqs. 7-9 runs: per-CTA max of w^2|chi|^2 with its lowest
+// linear cell index, plus p-norm partials.  chi is never written to memory
+// in the reduce modes.
 //
 // This replaces the zero-padded FFT correlation of Eq. 36 (Doppler-major:
 // one FFT pair per Doppler bin) with a delay-major transform: one L-point FFT
 // per (pair, delay) row, which is the form that keeps every operand on chip.
+#include <stdlib.h>
+
 #include "af_common.cuh"
 #include "af_kernels.h"
 
@@ -22,34 +26,60 @@ namespace af {
 
 constexpr int kThreads = 256;
 
+enum : int { MODE_REDUCE = 0, MODE_REDUCE_PNORM = 1, MODE_DUMP = 2 };
+
 template <typename K>
 __device__ __forceinline__ bool better(K a, long long ia, K b, long long ib) {
     return a > b || (a == b && ia < ib);
 }
 
-template <int L, typename C, typename K>
+__device__ __forceinline__ void pnorm_add(float hp, float kf, float& pv, float& ps) {
+    if (kf > pv) {
+        ps = (pv > 0.f ? ps * exp2f(hp * __log2f(pv / kf)) : 0.f) + 1.f;
+        pv = kf;
+    } else if (pv > 0.f) {
+        ps += exp2f(hp * __log2f(kf / pv));
+    }
+}
+
+__device__ __forceinline__ void pnorm_merge(float hp, float& pv, float& ps, float ov, float os) {
+    const float nv = fmaxf(pv, ov);
+    const float sa = (pv > 0.f) ? ps * exp2f(hp * __log2f(pv / nv)) : 0.f;
+    const float sb = (ov > 0.f) ? os * exp2f(hp * __log2f(ov / nv)) : 0.f;
+    pv = nv;
+    ps = sa + sb;
+}
+
+template <int L>
+__host__ __device__ constexpr int fold_len(int N) { return ((N + L - 1) / L) * L; }
+
+template <int L, int E, int MODE, typename C, typename K>
 __global__ void __launch_bounds__(kThreads)
 fwd_fft_kernel(const FwdArgs<C, K> a) {
-    using PL = Plan<L>;
+    using PL = Plan<L, E>;
     using T = decltype(C{}.x);
-    constexpr int TPR = PL::T;              // threads per row
+    constexpr int TPR = PL::T;               // threads per row
     constexpr int RS = kThreads / TPR;       // row slots per CTA
+    constexpr int RL = PL::radix(PL::passes - 1), NSL = PL::ns(PL::passes - 1), NBL = E / RL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* xs = reinterpret_cast<C*>(smem_raw);
-    C* hs = xs + a.N;
-    C* tws = hs + a.N;
-    C* bufs = tws + PL::tw_len;
+    const int N = a.N;
+    const int XS = fold_len<L>(N);
+    C* xs = reinterpret_cast<C*>(smem_raw);   // [XS]
+    C* hp = xs + XS;                          // [2N + XS], h_l(p) at hp[N + p]
+    C* tws = hp + 2 * N + XS;                 // [tw_len]
+    C* bufs = tws + PL::tw_len;               // [RS][padlen]
 
     const int tid = threadIdx.x;
     if (a.ctr_inc != nullptr && blockIdx.x == 0 && tid == 0) a.ctr_inc[0] += 1;
     const int pair = blockIdx.x / a.n_chunks;
     const int chunk = blockIdx.x - pair * a.n_chunks;
     const int m = pair / a.M, l = pair - m * a.M;
-    const int N = a.N;
 
-    for (int n = tid; n < N; n += kThreads) {
-        xs[n] = cmul(a.x[(size_t)m * N + n], a.pre[n]);
-        hs[n] = a.h[(size_t)l * N + n];
+    const C zero = mk((T)0, (T)0);
+    for (int n = tid; n < XS; n += kThreads) xs[n] = (n < N) ? cmul(a.x[(size_t)m * N + n], a.pre[n]) : zero;
+    for (int i = tid; i < 2 * N + XS; i += kThreads) {
+        const int p = i - N;
+        hp[i] = (p >= 0 && p < N) ? a.h[(size_t)l * N + p] : zero;
     }
     for (int i = tid; i < PL::tw_len; i += kThreads) tws[i] = a.tw[i];
 
@@ -57,8 +87,8 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     if (a.cdiag != nullptr && m == l && chunk == 0) {
         double sr = 0.0, si = 0.0;
         for (int n = tid; n < N; n += kThreads) {
-            C xv = a.x[(size_t)m * N + n], hv = a.h[(size_t)l * N + n];
-            double xr = xv.x, xi = xv.y, hr = hv.x, hi = hv.y;
+            const C xv = a.x[(size_t)m * N + n], hv = a.h[(size_t)l * N + n];
+            const double xr = xv.x, xi = xv.y, hr = hv.x, hi = hv.y;
             sr += xr * hr + xi * hi;
             si += xi * hr - xr * hi;
         }
@@ -82,202 +112,198 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     C* buf = bufs + slot * PL::padlen;
     const int d_begin = chunk * a.rows_per_chunk;
     const int d_end = min(a.D, d_begin + a.rows_per_chunk);
+    const int NF = XS / L;
+    const bool auto_pair = (m == l);
 
     K best = (K)-1;
-    long long best_idx = 0x7fffffffffffffffLL;
-    float pv = 0.f, ps = 0.f;                   // p-norm partials (key domain)
-    const bool auto_pair = (m == l);
+    int best_li = 0;                          // (d - d_begin) * L + bin
+    float pv = 0.f, ps = 0.f;                 // p-norm partials (key domain)
 
     for (int d0 = d_begin; d0 < d_end; d0 += RS) {
         const int d = d0 + slot;
         const bool row_in = d < d_end;
-        const int k = a.k_lo + d;
-        // ---- pass 0: lag products (folded mod L) + radix-16 butterflies ----
-        C v[16];
+        const int k = row_in ? a.k_lo + d : 0;
+        // ---- pass 0: lag products (folded mod L) + radix-E butterflies ----
+        C v[E];
+        const C* xk = xs + t;
+        const C* hk = hp + N + k + t;
+        if (NF == 1) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            C q = mk((T)0, (T)0);
-            if (row_in) {
-                for (int n = t + r * TPR; n < N; n += L) {
-                    const int p = n + k;
-                    if (p >= 0 && p < N) q = cadd(q, cmulc(xs[n], hs[p]));
-                }
+            for (int r = 0; r < E; ++r) v[r] = cmulc(xk[r * TPR], hk[r * TPR]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                C q = zero;
+                for (int c = 0; c < NF; ++c) q = cadd(q, cmulc(xk[r * TPR + c * L], hk[r * TPR + c * L]));
+                v[r] = q;
             }
-            v[r] = q;
         }
-        pass_compute<L, PL::radix(0), 1>(v, t, tws);
-        fft_rest<L, 1>(v, t, slot, buf, tws);
+        pass_compute<L, E, E, 1>(v, t, tws);
+        fft_rest<L, E, 1>(v, t, slot, buf, tws);
 
-        // ---- epilogue: chi(k, bin) is in registers ----
-        constexpr int RL = PL::radix(PL::passes - 1);
-        if (a.mode == FWD_DUMP) {
+        // ---- epilogue: chi(k, bin) is in registers, bins in increasing order ----
+        if constexpr (MODE == MODE_DUMP) {
             if (row_in) {
-                C* out = a.chi_out + ((size_t)pair * a.D + d) * L;
+                C* out = a.chi_out + ((size_t)pair * a.D + d) * L + t;
 #pragma unroll
-                for (int s = 0; s < 16 / RL; ++s)
+                for (int r = 0; r < RL; ++r)
 #pragma unroll
-                    for (int r = 0; r < RL; ++r) out[out_bin<L>(t, s, r)] = v[s * RL + r];
+                    for (int s = 0; s < NBL; ++s) out[TPR * s + r * NSL] = v[s * RL + r];
             }
         } else if (row_in && !(auto_pair && k == 0)) {
-            const long long row_base = ((long long)pair * a.D + d) * L;
+            const int lbase = (d - d_begin) * L + t;
+            const float* wrow = (a.weight_mode != WM_UNIFORM) ? a.wmap + (size_t)d * L + t : nullptr;
 #pragma unroll
-            for (int s = 0; s < 16 / RL; ++s) {
+            for (int r = 0; r < RL; ++r) {
 #pragma unroll
-                for (int r = 0; r < RL; ++r) {
-                    const int bin = out_bin<L>(t, s, r);
+                for (int s = 0; s < NBL; ++s) {
+                    const int off = TPR * s + r * NSL;
                     const C c = v[s * RL + r];
                     K key = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
-                    if (a.weight_mode != WM_UNIFORM) {
-                        const float w = __ldg(a.wmap + (size_t)d * L + bin);
+                    if (wrow != nullptr) {
+                        const float w = __ldg(wrow + off);
                         key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
                     }
-                    const long long cell = row_base + bin;
-                    if (better(key, cell, best, best_idx)) { best = key; best_idx = cell; }
-                    if (a.half_p > 0.f && key >= (K)0) {
-                        const float kf = (float)key;
-                        if (kf > pv) {
-                            ps = (pv > 0.f ? ps * exp2f(a.half_p * __log2f(pv / kf)) : 0.f) + 1.f;
-                            pv = kf;
-                        } else if (pv > 0.f) {
-                            ps += exp2f(a.half_p * __log2f(kf / pv));
-                        }
+                    if (key > best) { best = key; best_li = lbase + off; }
+                    if constexpr (MODE == MODE_REDUCE_PNORM) {
+                        if (key >= (K)0) pnorm_add(a.half_p, (float)key, pv, ps);
                     }
                 }
             }
         }
     }
 
-    if (a.mode == FWD_DUMP) return;
-
-    // ---- CTA reduction of (best, best_idx) and the p-norm partials ----
-    for (int o = 16; o > 0; o >>= 1) {
-        K ob = __shfl_xor_sync(0xffffffffu, best, o);
-        long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
-        if (better(ob, oi, best, best_idx)) { best = ob; best_idx = oi; }
-        if (a.half_p > 0.f) {
-            float ov = __shfl_xor_sync(0xffffffffu, pv, o);
-            float os = __shfl_xor_sync(0xffffffffu, ps, o);
-            float nv = fmaxf(pv, ov);
-            float sa = (pv > 0.f) ? ps * exp2f(a.half_p * __log2f(pv / nv)) : 0.f;
-            float sb = (ov > 0.f) ? os * exp2f(a.half_p * __log2f(ov / nv)) : 0.f;
-            pv = nv;
-            ps = sa + sb;
-        }
-    }
-    __shared__ K rk[kThreads / 32];
-    __shared__ long long ri[kThreads / 32];
-    __shared__ float rv[kThreads / 32], rsum[kThreads / 32];
-    const int warp = tid >> 5;
-    if ((tid & 31) == 0) { rk[warp] = best; ri[warp] = best_idx; rv[warp] = pv; rsum[warp] = ps; }
-    __syncthreads();
-    if (tid == 0) {
-        K b = rk[0];
-        long long bi = ri[0];
-        float vv = rv[0], ss = rsum[0];
-        for (int w = 1; w < kThreads / 32; ++w) {
-            if (better(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; }
-            if (a.half_p > 0.f) {
-                float nv = fmaxf(vv, rv[w]);
-                float sa = (vv > 0.f) ? ss * exp2f(a.half_p * __log2f(vv / nv)) : 0.f;
-                float sb = (rv[w] > 0.f) ? rsum[w] * exp2f(a.half_p * __log2f(rv[w] / nv)) : 0.f;
-                vv = nv;
-                ss = sa + sb;
+    if constexpr (MODE != MODE_DUMP) {
+        // ---- CTA reduction of (best, index) and the p-norm partials ----
+        long long best_idx = (best >= (K)0) ? ((long long)pair * a.D + d_begin) * L + best_li
+                                            : 0x7fffffffffffffffLL;
+        for (int o = 16; o > 0; o >>= 1) {
+            const K ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
+            if (better(ob, oi, best, best_idx)) { best = ob; best_idx = oi; }
+            if constexpr (MODE == MODE_REDUCE_PNORM) {
+                const float ov = __shfl_xor_sync(0xffffffffu, pv, o);
+                const float os = __shfl_xor_sync(0xffffffffu, ps, o);
+                pnorm_merge(a.half_p, pv, ps, ov, os);
             }
         }
-        a.pkey[blockIdx.x] = b;
-        a.pidx[blockIdx.x] = (b >= (K)0) ? bi : -1;
-        if (a.pvmax) { a.pvmax[blockIdx.x] = vv; a.psum[blockIdx.x] = ss; }
+        __shared__ K rk[kThreads / 32];
+        __shared__ long long ri[kThreads / 32];
+        __shared__ float rv[kThreads / 32], rsum[kThreads / 32];
+        const int warp = tid >> 5;
+        if ((tid & 31) == 0) { rk[warp] = best; ri[warp] = best_idx; rv[warp] = pv; rsum[warp] = ps; }
+        __syncthreads();
+        if (tid == 0) {
+            K b = rk[0];
+            long long bi = ri[0];
+            float vv = rv[0], ss = rsum[0];
+            for (int w = 1; w < kThreads / 32; ++w) {
+                if (better(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; }
+                if constexpr (MODE == MODE_REDUCE_PNORM) pnorm_merge(a.half_p, vv, ss, rv[w], rsum[w]);
+            }
+            a.pkey[blockIdx.x] = b;
+            a.pidx[blockIdx.x] = (b >= (K)0) ? bi : -1;
+            if (a.pvmax) { a.pvmax[blockIdx.x] = vv; a.psum[blockIdx.x] = ss; }
+        }
     }
 }
 
-template <int L, typename C, typename K>
+// ------------------------------------------------------------------ host ----
+template <int L, int E, typename C>
 static int smem_for(int N) {
-    return (int)sizeof(C) * (2 * N + Plan<L>::tw_len + (kThreads / Plan<L>::T) * Plan<L>::padlen);
+    using PL = Plan<L, E>;
+    const int XS = fold_len<L>(N);
+    return (int)sizeof(C) * (XS + 2 * N + XS + PL::tw_len + (kThreads / PL::T) * PL::padlen);
 }
 
-template <int L, typename C, typename K>
-static cudaError_t launch_L(const FwdArgs<C, K>& a, cudaStream_t s) {
-    const int smem = smem_for<L, C, K>(a.N);
-    auto kern = fwd_fft_kernel<L, C, K>;
+template <int L, int E, int MODE, typename C, typename K>
+static cudaError_t launch_LEM(const FwdArgs<C, K>& a, cudaStream_t s, bool prepare_only) {
+    const int smem = smem_for<L, E, C>(a.N);
+    auto kern = fwd_fft_kernel<L, E, MODE, C, K>;
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || prepare_only) return e;
     const int grid = a.M * a.M * a.n_chunks;
     kern<<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int L, typename C, typename K>
-static cudaError_t prepare_L(int N) {
-    return set_smem_once(reinterpret_cast<const void*>(fwd_fft_kernel<L, C, K>), smem_for<L, C, K>(N));
-}
-
-template <typename C, typename K>
-static cudaError_t prepare_any(int L, int N) {
-    switch (L) {
-        case 32: return prepare_L<32, C, K>(N);
-        case 64: return prepare_L<64, C, K>(N);
-        case 128: return prepare_L<128, C, K>(N);
-        case 256: return prepare_L<256, C, K>(N);
-        case 512: return prepare_L<512, C, K>(N);
-        case 1024: return prepare_L<1024, C, K>(N);
-        case 2048: return prepare_L<2048, C, K>(N);
-        case 4096: return prepare_L<4096, C, K>(N);
-        default: return cudaErrorInvalidValue;
+template <int L, int E, typename C, typename K>
+static cudaError_t launch_LE(const FwdArgs<C, K>& a, cudaStream_t s, bool prepare_only) {
+    if constexpr (sizeof(C) == sizeof(double2)) {
+        // FP64 acceptance pass: exact max only
+        return launch_LEM<L, E, MODE_REDUCE, C, K>(a, s, prepare_only);
+    } else {
+        if (prepare_only) {
+            cudaError_t e = launch_LEM<L, E, MODE_REDUCE, C, K>(a, s, true);
+            if (e == cudaSuccess) e = launch_LEM<L, E, MODE_REDUCE_PNORM, C, K>(a, s, true);
+            if (e == cudaSuccess) e = launch_LEM<L, E, MODE_DUMP, C, K>(a, s, true);
+            return e;
+        }
+        if (a.mode == FWD_DUMP) return launch_LEM<L, E, MODE_DUMP, C, K>(a, s, false);
+        if (a.half_p > 0.f) return launch_LEM<L, E, MODE_REDUCE_PNORM, C, K>(a, s, false);
+        return launch_LEM<L, E, MODE_REDUCE, C, K>(a, s, false);
     }
 }
 
-cudaError_t fft_prepare_f32(int L, int N) { return prepare_any<float2, float>(L, N); }
-cudaError_t fft_prepare_f64(int L, int N) { return prepare_any<double2, double>(L, N); }
-
 template <typename C, typename K>
-static cudaError_t launch_any(const FwdArgs<C, K>& a, cudaStream_t s) {
+static cudaError_t launch_any(const FwdArgs<C, K>& a, cudaStream_t s, bool prepare_only) {
+    const bool e8 = (a.fft_e == 8);
     switch (a.L) {
-        case 32: return launch_L<32>(a, s);
-        case 64: return launch_L<64>(a, s);
-        case 128: return launch_L<128>(a, s);
-        case 256: return launch_L<256>(a, s);
-        case 512: return launch_L<512>(a, s);
-        case 1024: return launch_L<1024>(a, s);
-        case 2048: return launch_L<2048>(a, s);
-        case 4096: return launch_L<4096>(a, s);
+        case 32: return e8 ? launch_LE<32, 8>(a, s, prepare_only) : launch_LE<32, 16>(a, s, prepare_only);
+        case 64: return e8 ? launch_LE<64, 8>(a, s, prepare_only) : launch_LE<64, 16>(a, s, prepare_only);
+        case 128: return e8 ? launch_LE<128, 8>(a, s, prepare_only) : launch_LE<128, 16>(a, s, prepare_only);
+        case 256: return e8 ? launch_LE<256, 8>(a, s, prepare_only) : launch_LE<256, 16>(a, s, prepare_only);
+        case 512: return e8 ? launch_LE<512, 8>(a, s, prepare_only) : launch_LE<512, 16>(a, s, prepare_only);
+        case 1024: return e8 ? launch_LE<1024, 8>(a, s, prepare_only) : launch_LE<1024, 16>(a, s, prepare_only);
+        case 2048: return e8 ? launch_LE<2048, 8>(a, s, prepare_only) : launch_LE<2048, 16>(a, s, prepare_only);
+        case 4096: return e8 ? launch_LE<4096, 8>(a, s, prepare_only) : launch_LE<4096, 16>(a, s, prepare_only);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s) { return launch_any(a, s); }
-cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s) { return launch_any(a, s); }
+cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s) { return launch_any(a, s, false); }
+cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s) { return launch_any(a, s, false); }
 
-template <typename C>
+cudaError_t fft_prepare_f32(int L, int N, int E) {
+    FwdArgs<float2, float> a{};
+    a.L = L; a.N = N; a.fft_e = E;
+    return launch_any(a, nullptr, true);
+}
+cudaError_t fft_prepare_f64(int L, int N, int E) {
+    FwdArgs<double2, double> a{};
+    a.L = L; a.N = N; a.fft_e = E;
+    return launch_any(a, nullptr, true);
+}
+
+template <typename C, int E>
 static int smem_any(int L, int N) {
     switch (L) {
-        case 32: return smem_for<32, C, float>(N);
-        case 64: return smem_for<64, C, float>(N);
-        case 128: return smem_for<128, C, float>(N);
-        case 256: return smem_for<256, C, float>(N);
-        case 512: return smem_for<512, C, float>(N);
-        case 1024: return smem_for<1024, C, float>(N);
-        case 2048: return smem_for<2048, C, float>(N);
-        case 4096: return smem_for<4096, C, float>(N);
+        case 32: return smem_for<32, E, C>(N);
+        case 64: return smem_for<64, E, C>(N);
+        case 128: return smem_for<128, E, C>(N);
+        case 256: return smem_for<256, E, C>(N);
+        case 512: return smem_for<512, E, C>(N);
+        case 1024: return smem_for<1024, E, C>(N);
+        case 2048: return smem_for<2048, E, C>(N);
+        case 4096: return smem_for<4096, E, C>(N);
         default: return -1;
     }
 }
 
-int fft_smem_bytes(int L, int N, bool fp64) { return fp64 ? smem_any<double2>(L, N) : smem_any<float2>(L, N); }
+int fft_smem_bytes(int L, int N, bool fp64, int E) {
+    if (E == 8) return fp64 ? smem_any<double2, 8>(L, N) : smem_any<float2, 8>(L, N);
+    return fp64 ? smem_any<double2, 16>(L, N) : smem_any<float2, 16>(L, N);
+}
 
-int fft_rows_per_cta(int L) { return (L >= 32 && L <= 4096) ? kThreads / (L / 16) : 0; }
+int fft_rows_per_cta(int L, int E) { return (L >= 2 * E && L <= 4096) ? kThreads / (L / E) : 0; }
 
-int fft_tw_len(int L) {
-    switch (L) {
-        case 32: return Plan<32>::tw_len;
-        case 64: return Plan<64>::tw_len;
-        case 128: return Plan<128>::tw_len;
-        case 256: return Plan<256>::tw_len;
-        case 512: return Plan<512>::tw_len;
-        case 1024: return Plan<1024>::tw_len;
-        case 2048: return Plan<2048>::tw_len;
-        case 4096: return Plan<4096>::tw_len;
-        default: return -1;
+int fft_default_elems(int L, bool fp64) {
+    if (const char* e = getenv("SQNGD_FFT_E")) {
+        const int v = atoi(e);
+        if ((v == 8 || v == 16) && L >= 2 * v) return v;
     }
+    if (fp64) return 8;
+    return (L >= 512) ? 8 : 16;
 }
 
 }  // namespace af

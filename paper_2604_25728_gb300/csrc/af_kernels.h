@@ -41,19 +41,22 @@ struct FwdArgs {
     double2* cdiag;        // [M] chi_mm(0,0) = sum_n x_m conj(h_m), FP64 (may be nullptr)
     C* chi_out;            // FWD_DUMP output
     long long* ctr_inc;    // if set, CTA 0 adds 1 to ctr_inc[0] (outer-iteration counter)
+    int fft_e;             // FFT path: values per thread (8 or 16); selects the twiddle plan
 };
 
-// FFT path: returns the dynamic shared memory bytes, or -1 if L unsupported.
-int fft_smem_bytes(int L, int N, bool fp64);
-int fft_rows_per_cta(int L);
-int fft_tw_len(int L);
+// FFT path with E values per thread: dynamic shared memory bytes (-1 if L
+// unsupported), row slots per 256-thread CTA, and the default E for L.
+int fft_smem_bytes(int L, int N, bool fp64, int E);
+int fft_rows_per_cta(int L, int E);
+int fft_default_elems(int L, bool fp64);
 cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
 cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
+cudaError_t fft_prepare_f32(int L, int N, int E);
+cudaError_t fft_prepare_f64(int L, int N, int E);
 
-// Raise the dynamic shared-memory limit of the kernels a context will use
-// (FP32 forward: FFT or DFT; FP64 acceptance: FFT or DFT).
-cudaError_t fwd_prepare(bool fft, int L, int N);
-cudaError_t acc_prepare(bool fft, int L, int N);
+// Raise the dynamic shared-memory limit of the DFT kernels a context will use.
+cudaError_t dft_prepare_f32(int N);
+cudaError_t dft_prepare_f64(int N);
 
 // Direct DFT path (any grid), SIMT.
 int dft_rows_per_cta();

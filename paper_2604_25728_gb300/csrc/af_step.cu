@@ -47,12 +47,33 @@ __device__ __forceinline__ int upper_bound_f(const float* v, int n, float x) {
     return lo;
 }
 
+// Number of thresholds <= v (upper bound).  For the uniform set
+// rho_i = (i + 1/2)/K the answer is within one of floor(K v + 1/2); the table
+// is then consulted at most twice, so the count is exact for any v.
+__device__ __forceinline__ int count_le(const QuantArgs& q, float v) {
+    if (!q.uniform) return upper_bound_f(q.rho, q.K, v);
+    int c = (int)floorf(fminf(fmaxf(v, -1.f), 2.f) * (float)q.K + 0.5f);
+    c = min(max(c, 0), q.K);
+    if (c > 0 && __ldg(q.rho + c - 1) > v) --c;
+    else if (c < q.K && __ldg(q.rho + c) <= v) ++c;
+    return c;
+}
+// Number of thresholds < v (lower bound), same scheme.
+__device__ __forceinline__ int count_lt(const QuantArgs& q, float v) {
+    if (!q.uniform) return lower_bound_f(q.rho, q.K, v);
+    int c = (int)ceilf(fminf(fmaxf(v, -1.f), 2.f) * (float)q.K - 0.5f);
+    c = min(max(c, 0), q.K);
+    if (c > 0 && __ldg(q.rho + c - 1) >= v) --c;
+    else if (c < q.K && __ldg(q.rho + c) < v) ++c;
+    return c;
+}
+
 // Soft quantizer of Eq. 24 at z.  Thresholds more than `win` below z have
 // tanh = +1 and those more than `win` above have tanh = -1 in FP32, so only
 // the window is evaluated; the saturated ones add 2a each = i0 / B.
 __device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, float* dydz, float2* x) {
-    const int i0 = lower_bound_f(q.rho, q.K, z - q.win);
-    const int i1 = upper_bound_f(q.rho, q.K, z + q.win);
+    const int i0 = count_lt(q, z - q.win);
+    const int i1 = count_le(q, z + q.win);
     float s = 0.f, ds = 0.f;
     for (int i = i0; i < i1; ++i) {
         const float t = tanhf(q.c * (z - q.rho[i]));
@@ -71,7 +92,7 @@ __device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, fl
     }
 }
 
-__device__ __forceinline__ int hard_q(const QuantArgs& q, float z) { return upper_bound_f(q.rho, q.K, z); }
+__device__ __forceinline__ int hard_q(const QuantArgs& q, float z) { return count_le(q, z); }
 
 // ------------------------------------------------------------ wave kernels --
 __global__ void wave_from_logits_kernel(const float* __restrict__ u, int n, QuantArgs q, int hard,
@@ -175,6 +196,9 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const FinArgs a) {
     __shared__ double2 s_g;          // sparse coefficient g
     __shared__ int s_cell[4];        // m*, l*, k*, j*  (m* = -1: no sparse term)
     __shared__ float s_adam[3];
+    __shared__ float2 s_G;           // SNRL coefficient of this row
+    __shared__ float s_scale;        // projection factor
+    __shared__ int s_ok;             // best-design decision
 
     // ---- 1. merge the forward partials per class --------------------------
     float kb[2] = {-1.f, -1.f};
@@ -286,19 +310,19 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const FinArgs a) {
             if (mag > 0.0) s_g = make_double2(a.eps * w * cr / mag, a.eps * w * ci / mag);
         }
     }
-    __syncthreads();
-    const float2 g = make_float2((float)s_g.x, (float)s_g.y);
-
-    // SNRL coefficient G_m = (1-eps)(2/M)(p_m - p_tar)/N * c_m/|c_m|
-    float2 Gm = make_float2(0.f, 0.f);
-    {
+    // SNRL coefficient G_m = (1-eps)(2/M)(p_m - p_tar)/N * c_m/|c_m| (FP64, once)
+    if (tid == 0) {
         const double2 c = a.cdiag[m];
         const double mag = sqrt(c.x * c.x + c.y * c.y);
+        s_G = make_float2(0.f, 0.f);
         if (mag > 0.0) {
             const double coef = (1.0 - a.eps) * (2.0 / M) * (mag / N - a.ptar) / N / mag;
-            Gm = make_float2((float)(coef * c.x), (float)(coef * c.y));
+            s_G = make_float2((float)(coef * c.x), (float)(coef * c.y));
         }
     }
+    __syncthreads();
+    const float2 g = make_float2((float)s_g.x, (float)s_g.y);
+    const float2 Gm = s_G;
 
     // ---- 3. row m of the gradient ------------------------------------------
     float2 gx[kMaxPerThread], gh[kMaxPerThread];
@@ -367,8 +391,9 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const FinArgs a) {
     if (tid == 0) {
         const long long t = (a.mode == FIN_ADAM_H) ? a.ctr[1] + o * a.n_h + a.inner + 1
                                                    : a.ctr[2] + o * a.n_x + a.inner + 1;
-        s_adam[0] = (float)(1.0 - pow((double)a.b1, (double)t));
-        s_adam[1] = (float)(1.0 - pow((double)a.b2, (double)t));
+        // 1 - beta^t = -expm1(t ln beta), FP32 (relative error ~1e-6 at any t)
+        s_adam[0] = -expm1f((float)t * log1pf(a.b1 - 1.f));
+        s_adam[1] = -expm1f((float)t * log1pf(a.b2 - 1.f));
     }
     __syncthreads();
     const float c1 = s_adam[0], c2 = s_adam[1];
@@ -378,13 +403,25 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const FinArgs a) {
         if (a.snap_best) {
             const double* prev = a.best2 + ((o + 1) & 1) * 4;
             double* cur = a.best2 + (o & 1) * 4;
-            double smax = -1e300;
-            for (int mm = 0; mm < M; ++mm) {
-                const double2 c = a.cdiag[mm];
-                const double p = sqrt(c.x * c.x + c.y * c.y) / (double)N;
-                smax = fmax(smax, -20.0 * log10(p));
+            // SNRL_m = -20 log10 p_m <= target + 0.05 dB  <=>  p_m^2 >= p_min^2
+            if (tid == 0) {
+                double pmin2 = 1e300;
+                for (int mm = 0; mm < M; ++mm) {
+                    const double2 c = a.cdiag[mm];
+                    pmin2 = fmin(pmin2, (c.x * c.x + c.y * c.y) / ((double)N * N));
+                }
+                s_ok = (pmin2 >= a.p_accept2 && s_terms[1] < prev[0]) ? 1 : 0;
+                if (m == 0) {
+                    if (s_ok) {
+                        cur[0] = s_terms[1]; cur[1] = s_terms[0];
+                        cur[2] = (double)(a.ctr[3] + o); cur[3] = -10.0 * log10(pmin2);
+                    } else {
+                        for (int i = 0; i < 4; ++i) cur[i] = prev[i];
+                    }
+                }
             }
-            const bool ok = smax <= a.snrl_db + 0.05 && s_terms[1] < prev[0];
+            __syncthreads();
+            const bool ok = s_ok != 0;
             if (ok) {
                 for (int i = 0; i < nper; ++i) {
                     const int n = tid + i * kFinThreads;
@@ -392,14 +429,6 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const FinArgs a) {
                     const size_t e = (size_t)m * N + n;
                     if (a.best_h) a.best_h[e] = a.h[e];
                     if (a.best_q) a.best_q[e] = hard_q(a.qa, sigmoidf_(a.u[e]));
-                }
-            }
-            if (m == 0 && tid == 0) {
-                if (ok) {
-                    cur[0] = s_terms[1]; cur[1] = s_terms[0];
-                    cur[2] = (double)(a.ctr[3] + o); cur[3] = smax;
-                } else {
-                    for (int i = 0; i < 4; ++i) cur[i] = prev[i];
                 }
             }
         }
@@ -425,7 +454,9 @@ __global__ void __launch_bounds__(kFinThreads) fin_kernel(const FinArgs a) {
             e2 += (double)hv.x * hv.x + (double)hv.y * hv.y;
         }
         e2 = block_sum_d(e2, shd);
-        const float sc = (e2 > 0.0) ? (float)sqrt((double)N / e2) : 1.f;
+        if (tid == 0) s_scale = (e2 > 0.0) ? (float)sqrt((double)N / e2) : 1.f;
+        __syncthreads();
+        const float sc = s_scale;
         bool bad = !isfinite(sc);
 #pragma unroll
         for (int i = 0; i < kMaxPerThread; ++i) {

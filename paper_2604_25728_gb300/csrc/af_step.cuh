@@ -13,6 +13,7 @@ struct QuantArgs {
     float a, c;           // a = 1/(2B), sharpness c
     float win;            // half window (in z units) outside which tanh is +-1 in FP32
     const float2* level;  // [B] e^{j 2 pi b / B}, FP64-built
+    int uniform;          // rho_i = (i + 1/2)/K: indices can be found arithmetically
 };
 
 enum FinMode : int {
@@ -77,6 +78,7 @@ struct FinArgs {
     int32_t* best_q;
     float2* best_h;
     double snrl_db;
+    double p_accept2;         // (10^{-(snrl_db + 0.05)/20})^2: a design is acceptable when min p_m^2 >= this
 };
 
 struct AccArgs {

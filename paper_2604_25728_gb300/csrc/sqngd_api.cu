@@ -27,11 +27,11 @@ inline void phasor(double t, double* re, double* im) {
 
 struct FftPassInfo { int R, NS; };
 
-// Host mirror of the device FFT plan (radix 16 passes, then the remainder).
-std::vector<FftPassInfo> fft_plan(int L) {
+// Host mirror of the device FFT plan (radix-E passes, then the remainder).
+std::vector<FftPassInfo> fft_plan(int L, int E) {
     std::vector<FftPassInfo> p;
     int rem = L, ns = 1;
-    while (rem >= 16 && rem % 16 == 0) { p.push_back({16, ns}); ns *= 16; rem /= 16; }
+    while (rem >= E && rem % E == 0) { p.push_back({E, ns}); ns *= E; rem /= E; }
     if (rem > 1) p.push_back({rem, ns});
     return p;
 }
@@ -73,6 +73,8 @@ struct af_ctx {
     // workspace
     int n_chunks = 0, rows_per_chunk = 0, nblk = 0, ctas_per_pair = 0;
     bool acc_fft = false;
+    bool rho_uniform = true;   // thresholds are the default (i + 1/2)/K
+    int fft_e = 0, acc_e = 0;  // FFT values per thread: FP32 path, FP64 acceptance
     int acc_n_chunks = 0, acc_rows_per_chunk = 0, acc_nblk = 0, acc_ctas_per_pair = 0;
     float* pkey = nullptr;
     long long* pidx = nullptr;
@@ -146,6 +148,7 @@ static QuantArgs quant_args(const af_ctx* c) {
     q.c = (float)c->cfg.c;
     q.win = (float)(12.0 / c->cfg.c);
     q.level = c->level;
+    q.uniform = c->rho_uniform ? 1 : 0;
     return q;
 }
 
@@ -235,7 +238,8 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     bool uniform = (L >= 32 && L <= 4096 && (L & (L - 1)) == 0);
     for (int j = 0; uniform && j < L; ++j)
         if (fabs(c->nu[j] - (c->nu0 + (double)j / L)) > 1e-12) uniform = false;
-    const int fft_smem = uniform ? fft_smem_bytes(L, N, false) : -1;
+    c->fft_e = uniform ? fft_default_elems(L, false) : 0;
+    const int fft_smem = uniform ? fft_smem_bytes(L, N, false, c->fft_e) : -1;
     uniform = uniform && fft_smem > 0 && fft_smem <= 227 * 1024;
     if (cfg->path == AF_PATH_FFT && !uniform) {
         c->err = "AF_PATH_FFT needs nu_j = nu_0 + j/L with L a power of two in 32..4096";
@@ -243,6 +247,12 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     }
     c->path = (cfg->path == AF_PATH_AUTO) ? (uniform ? AF_PATH_FFT : AF_PATH_DFT) : cfg->path;
     c->grid_fft = uniform;
+    // FP64 acceptance pass: FFT when it fits in shared memory
+    c->acc_e = c->grid_fft ? fft_default_elems(L, true) : 0;
+    {
+        const int smem64 = c->grid_fft ? fft_smem_bytes(L, N, true, c->acc_e) : -1;
+        c->acc_fft = c->grid_fft && smem64 > 0 && smem64 <= 227 * 1024;
+    }
 
     af_status s;
     // ---- tables, built in FP64 ----
@@ -268,22 +278,26 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     if ((s = upload(c, &c->pre, pre)) || (s = upload(c, &c->pre64, pre64)) || (s = upload(c, &c->wL, wL)) ||
         (s = upload(c, &c->level, lev)) || (s = upload(c, &c->level64, lev64)))
         return fail(s);
-    if (c->grid_fft) {
-        std::vector<float2> tw;
-        std::vector<double2> tw64;
-        const auto plan = fft_plan(L);
+    // Stockham twiddles: for every pass p >= 1 a table [R][NS] of e^{+j 2 pi r k / (NS R)}
+    auto twiddles = [&](int E, std::vector<double2>& out) {
+        const auto plan = fft_plan(L, E);
         for (size_t p = 1; p < plan.size(); ++p) {
             const int R = plan[p].R, NS = plan[p].NS;
             for (int r = 0; r < R; ++r)
                 for (int k = 0; k < NS; ++k) {
                     double re, im;
                     phasor((double)r * k / ((double)NS * R), &re, &im);
-                    tw.push_back(make_float2((float)re, (float)im));
-                    tw64.push_back(make_double2(re, im));
+                    out.push_back(make_double2(re, im));
                 }
         }
-        if ((int)tw.size() != fft_tw_len(L)) { c->err = "internal: FFT twiddle table size mismatch"; return fail(AF_ERR_CUDA); }
-        if ((s = upload(c, &c->tw, tw)) || (s = upload(c, &c->tw64, tw64))) return fail(s);
+    };
+    if (c->grid_fft) {
+        std::vector<double2> t32, t64;
+        twiddles(c->fft_e, t32);
+        twiddles(c->acc_e, t64);
+        std::vector<float2> tw(t32.size());
+        for (size_t i = 0; i < t32.size(); ++i) tw[i] = make_float2((float)t32[i].x, (float)t32[i].y);
+        if ((s = upload(c, &c->tw, tw)) || (s = upload(c, &c->tw64, t64))) return fail(s);
     }
     {
         // phasor table of the arbitrary-grid path (also used for acceptance when
@@ -311,15 +325,14 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
 
     // kernels' shared-memory limits are raised here, outside any graph capture
     {
-        cudaError_t e = fwd_prepare(c->path == AF_PATH_FFT, L, N);
-        if (e == cudaSuccess) e = acc_prepare(c->grid_fft && fft_smem_bytes(L, N, true) > 0 &&
-                                                  fft_smem_bytes(L, N, true) <= 227 * 1024, L, N);
+        cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e) : dft_prepare_f32(N);
+        if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
         if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
     }
 
     // ---- launch geometry and workspace ----
     if (c->path == AF_PATH_FFT) {
-        const int RS = fft_rows_per_cta(L);
+        const int RS = fft_rows_per_cta(L, c->fft_e);
         int it = (int)lround((double)c->P * c->D / ((double)RS * 152 * 6));
         if (it < 1) it = 1;
         if (const char* e = getenv("SQNGD_FFT_ROW_ITERS")) it = atoi(e) > 0 ? atoi(e) : it;
@@ -332,11 +345,8 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         c->ctas_per_pair = c->n_chunks * dft_col_tiles(L);
     }
     c->nblk = c->P * c->ctas_per_pair;
-    // FP64 acceptance pass geometry
-    const int smem64 = c->grid_fft ? fft_smem_bytes(L, N, true) : -1;
-    c->acc_fft = c->grid_fft && smem64 > 0 && smem64 <= 227 * 1024;
     if (c->acc_fft) {
-        const int RS = fft_rows_per_cta(L);
+        const int RS = fft_rows_per_cta(L, c->acc_e);
         int it = (c->P * c->D) / (RS * 152 * 4);
         if (it < 1) it = 1;
         c->acc_rows_per_chunk = RS * it;
@@ -401,6 +411,8 @@ extern "C" af_status af_set_thresholds(af_ctx* c, const float* rho_host) {
     }
     CK(c, cudaStreamSynchronize(c->stream));
     CK(c, cudaMemcpy(c->rho, rho_host, sizeof(float) * c->K, cudaMemcpyHostToDevice));
+    c->rho_uniform = false;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     return AF_OK;
 }
 
@@ -417,6 +429,7 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
     a.half_p = (float)(c->cfg.pnorm * 0.5);
     a.pkey = c->pkey; a.pidx = c->pidx; a.pvmax = c->pvmax; a.psum = c->psum;
     a.cdiag = c->cdiag;
+    a.fft_e = c->fft_e;
     return a;
 }
 
@@ -440,6 +453,10 @@ static FinArgs fin_args(af_ctx* c) {
     f.err_flag = c->errflag;
     f.qa = quant_args(c);
     f.snrl_db = c->cfg.snrl_db;
+    {
+        const double p = pow(10.0, -(c->cfg.snrl_db + 0.05) / 20.0);
+        f.p_accept2 = p * p;
+    }
     f.n_h = c->cfg.n_h; f.n_x = c->cfg.n_x;
     f.evals_per_outer = c->cfg.n_h + c->cfg.n_x;
     f.lr = 0.f;
@@ -662,6 +679,7 @@ extern "C" af_status af_eval_hard(af_ctx* c, const float* u, const float* h, dou
     a.half_p = 0.f;
     a.pkey = c->pkey64; a.pidx = c->pidx64;
     a.cdiag = c->cdiag;
+    a.fft_e = c->acc_e;
     CK(c, c->acc_fft ? launch_fwd_fft_f64(a, c->stream) : launch_fwd_dft_f64(a, c->stream));
     AccArgs g{};
     g.M = M; g.N = N; g.nblk = c->acc_nblk; g.ctas_per_pair = c->acc_ctas_per_pair;

@@ -59,8 +59,11 @@ FFT_CASES = [
 ]
 
 
+@pytest.mark.parametrize("elems", ["8", "16"])
 @pytest.mark.parametrize("case", FFT_CASES)
-def test_ambiguity_fft_matches_oracle(api, orc, case):
+def test_ambiguity_fft_matches_oracle(api, orc, case, elems, monkeypatch):
+    """Both register-FFT shapes (8 or 16 values per thread) against the oracle."""
+    monkeypatch.setenv("SQNGD_FFT_E", elems)
     M, N, L, k_lo, k_hi, nu0 = case
     nu = nu0 + np.arange(L) / L
     x, h = _pair(orc, 100 + N, M, N)
@@ -421,3 +424,21 @@ def test_sqngd_tiny_run_tracks_oracle_statistically(api, orc):
         start, _ = orc.metrics(np.exp(2j * np.pi * b / w.B), h0, w.nu, w.k_lo, w.k_hi)
         assert out[2] < start[2] and met[2] < start[2]
     assert abs(np.median(g_final) - np.median(o_final)) <= 0.5, (g_final, o_final)
+
+
+def test_quantize_with_user_thresholds_bit_exact(api, orc):
+    """Non-uniform thresholds (af_set_thresholds) take the binary-search path."""
+    B, r_n = 8, 5
+    K = B * r_n
+    rho = np.sort(wl.uniform(23, K, 1)).astype(np.float32)
+    z = np.concatenate([wl.uniform(24, 5000, 1).astype(np.float32), rho,
+                        np.nextafter(rho, np.float32(0))]).astype(np.float32)
+    ctx = _ctx(api, 1, 8, B, wl.full_grid(32), -7, 7, r_n=r_n)
+    ctx.af_set_thresholds(rho)
+    q, _ = ctx.quantize(_dev(z))
+    y, dy, _ = ctx.soft_quantize(_dev(z))
+    ctx.af_sync()
+    oq, _ = orc.hard_quantize(z.astype(np.float64), rho.astype(np.float64), B)
+    np.testing.assert_array_equal(q.cpu().numpy(), oq)
+    oy, ody = orc.soft_quantize(z.astype(np.float64), rho.astype(np.float64), 1.0 / (2 * B), 300.0)
+    assert np.max(np.abs(y.cpu().numpy() - oy)) <= 2e-5
