@@ -104,9 +104,10 @@ template <int L, int E> struct Plan {
     static constexpr int passes = nfull + (rem > 1 ? 1 : 0);
     static constexpr int radix(int p) { return p < nfull ? E : rem; }
     static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * radix(p - 1); }
-    // offset of pass p's twiddle table [R][NS] (pass 0 has none)
-    static constexpr int tw_off(int p) { return p <= 1 ? 0 : tw_off(p - 1) + radix(p - 1) * ns(p - 1); }
-    static constexpr int tw_len = tw_off(passes - 1) + radix(passes - 1) * ns(passes - 1);
+    // offset of pass p's twiddle table [R-1][NS] for r = 1..R-1 (row r = 0 is all
+    // ones and is not stored; pass 0 has no table)
+    static constexpr int tw_off(int p) { return p <= 1 ? 0 : tw_off(p - 1) + (radix(p - 1) - 1) * ns(p - 1); }
+    static constexpr int tw_len = tw_off(passes - 1) + (radix(passes - 1) - 1) * ns(passes - 1);
     static constexpr int padlen = L + L / E;       // row buffer with one pad slot per E
 };
 
@@ -123,7 +124,7 @@ __device__ __forceinline__ void pass_compute(C (&v)[E], int t, const C* tw) {
         if constexpr (NS > 1) {
             const C* tk = tw + ((t + T * s) & (NS - 1));
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[s * R + r] = cmul(v[s * R + r], tk[r * NS]);
+            for (int r = 1; r < R; ++r) v[s * R + r] = cmul(v[s * R + r], tk[(r - 1) * NS]);
         }
         Dft<R, 1>::run(&v[s * R]);
     }

@@ -1,0 +1,143 @@
+// af_device.cuh -- device helpers shared by the per-step kernels: sigmoid,
+// threshold counting, the quantizers of Eqs. 24 and 43, block reductions.
+#pragma once
+
+#include <math.h>
+
+#include "af_common.cuh"
+#include "af_step.cuh"
+
+namespace af {
+
+__device__ __forceinline__ float sigmoidf_(float u) { return 1.f / (1.f + expf(-u)); }
+
+__device__ __forceinline__ int lower_bound_f(const float* v, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (v[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int upper_bound_f(const float* v, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (v[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Number of thresholds <= v (upper bound).  For the uniform set
+// rho_i = (i + 1/2)/K the answer is within one of floor(K v + 1/2); the table
+// is then consulted at most twice, so the count is exact for any v.
+__device__ __forceinline__ int count_le(const QuantArgs& q, float v) {
+    if (!q.uniform) return upper_bound_f(q.rho, q.K, v);
+    int c = (int)floorf(fminf(fmaxf(v, -1.f), 2.f) * (float)q.K + 0.5f);
+    c = min(max(c, 0), q.K);
+    if (c > 0 && __ldg(q.rho + c - 1) > v) --c;
+    else if (c < q.K && __ldg(q.rho + c) <= v) ++c;
+    return c;
+}
+// Number of thresholds < v (lower bound), same scheme.
+__device__ __forceinline__ int count_lt(const QuantArgs& q, float v) {
+    if (!q.uniform) return lower_bound_f(q.rho, q.K, v);
+    int c = (int)ceilf(fminf(fmaxf(v, -1.f), 2.f) * (float)q.K - 0.5f);
+    c = min(max(c, 0), q.K);
+    if (c > 0 && __ldg(q.rho + c - 1) >= v) --c;
+    else if (c < q.K && __ldg(q.rho + c) < v) ++c;
+    return c;
+}
+
+// Soft quantizer of Eq. 24 at z.  Thresholds more than `win` below z have
+// tanh = +1 and those more than `win` above have tanh = -1 in FP32, so only
+// the window is evaluated; the saturated ones add 2a each = i0 / B.
+//
+// Uniform thresholds rho_i = (i + 1/2)/K: with e_i = e^{2c(z - rho_i)},
+// tanh(c(z - rho_i)) = 1 - 2/(1 + e_i) and 1 - tanh^2 = 4 e_i/(1 + e_i)^2, and
+// e_{i+1} = e_i e^{-2c/K}.  The sum is taken outward from the threshold
+// nearest z (where tanh is not saturated and the recursion has taken no
+// steps), each e_i by one multiply; the terms far from z, where the
+// accumulated rounding of the recursion grows, are saturated.
+__device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, float* dydz, float2* x) {
+    const int i0 = count_lt(q, z - q.win);
+    const int i1 = count_le(q, z + q.win);
+    float s = 0.f, ds = 0.f;
+    if (q.uniform) {
+        if (i1 > i0) {
+            const float invK = 1.f / (float)q.K;
+            const int ic = min(max((int)floorf(z * (float)q.K), i0), i1 - 1);
+            const float c2 = 2.f * q.c;
+            const float r_up = expf(-c2 * invK);         // e_{i+1} / e_i
+            const float r_dn = expf(c2 * invK);          // e_{i-1} / e_i
+            float sum_inv = 0.f, sum_d = 0.f;            // sum 1/(1+e), sum e/(1+e)^2
+            float e = expf(c2 * (z - ((float)ic + 0.5f) * invK));
+            for (int i = ic; i < i1; ++i) {
+                const float inv = __frcp_rn(1.f + e);
+                sum_inv += inv;
+                sum_d = fmaf(e * inv, inv, sum_d);
+                e *= r_up;
+            }
+            e = expf(c2 * (z - ((float)ic - 0.5f) * invK));
+            for (int i = ic - 1; i >= i0; --i) {
+                const float inv = __frcp_rn(1.f + e);
+                sum_inv += inv;
+                sum_d = fmaf(e * inv, inv, sum_d);
+                e *= r_dn;
+            }
+            // sum a (tanh + 1) = a (2 W - 2 sum_inv);  sum a c (1 - tanh^2) = 4 a c sum_d
+            s = 2.f * q.a * ((float)(i1 - i0) - sum_inv);
+            ds = 4.f * q.a * q.c * sum_d;
+        }
+    } else {
+        for (int i = i0; i < i1; ++i) {
+            const float t = tanhf(q.c * (z - q.rho[i]));
+            s += q.a * (t + 1.f);
+            ds += q.a * q.c * (1.f - t * t);
+        }
+    }
+    if (y) *y = (float)i0 * (2.f * q.a) + s;
+    if (dydz) *dydz = ds;
+    if (x) {
+        // phase in cycles: i0/B + s, reduced modulo 1 before sincospi
+        float f = (float)(i0 % q.B) / (float)q.B + s;
+        f -= floorf(f);
+        float sn, cs;
+        sincospif(2.f * f, &sn, &cs);
+        *x = make_float2(cs, sn);
+    }
+}
+
+__device__ __forceinline__ int hard_q(const QuantArgs& q, float z) { return count_le(q, z); }
+
+// ------------------------------------------------------- block reductions --
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    return t;
+}
+
+__device__ __forceinline__ bool fbetter(float a, long long ia, float b, long long ib) {
+    return a > b || (a == b && ia < ib);
+}
+
+__device__ __forceinline__ void pmerge(float hp, float& v, float& s, float ov, float os) {
+    if (ov <= 0.f) return;
+    if (v <= 0.f) { v = ov; s = os; return; }
+    const float nv = fmaxf(v, ov);
+    s = s * exp2f(hp * __log2f(v / nv)) + os * exp2f(hp * __log2f(ov / nv));
+    v = nv;
+}
+
+}  // namespace af

@@ -132,6 +132,7 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
 
     K best = (K)-1;
     long long best_idx = 0x7fffffffffffffffLL;
+    C best_c = mk((T)0, (T)0);
     float pv = 0.f, ps = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -149,7 +150,7 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
                 key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
             }
             const long long cell = ((long long)pair * a.D + d) * L + j;
-            if (dbetter(key, cell, best, best_idx)) { best = key; best_idx = cell; }
+            if (dbetter(key, cell, best, best_idx)) { best = key; best_idx = cell; best_c = v; }
             if (a.half_p > 0.f && key >= (K)0) {
                 const float kf = (float)key;
                 if (kf > pv) {
@@ -164,7 +165,9 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
     for (int o = 16; o > 0; o >>= 1) {
         K ob = __shfl_xor_sync(0xffffffffu, best, o);
         long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
-        if (dbetter(ob, oi, best, best_idx)) { best = ob; best_idx = oi; }
+        const T ocx = __shfl_xor_sync(0xffffffffu, best_c.x, o);
+        const T ocy = __shfl_xor_sync(0xffffffffu, best_c.y, o);
+        if (dbetter(ob, oi, best, best_idx)) { best = ob; best_idx = oi; best_c = mk(ocx, ocy); }
         if (a.half_p > 0.f) {
             float ov = __shfl_xor_sync(0xffffffffu, pv, o);
             float os = __shfl_xor_sync(0xffffffffu, ps, o);
@@ -177,16 +180,18 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
     }
     __shared__ K rk[kDftThreads / 32];
     __shared__ long long ri[kDftThreads / 32];
+    __shared__ C rc[kDftThreads / 32];
     __shared__ float rv[kDftThreads / 32], rsum[kDftThreads / 32];
     const int warp = tid >> 5;
-    if ((tid & 31) == 0) { rk[warp] = best; ri[warp] = best_idx; rv[warp] = pv; rsum[warp] = ps; }
+    if ((tid & 31) == 0) { rk[warp] = best; ri[warp] = best_idx; rc[warp] = best_c; rv[warp] = pv; rsum[warp] = ps; }
     __syncthreads();
     if (tid == 0) {
         K b = rk[0];
         long long bi = ri[0];
+        C bc = rc[0];
         float vv = rv[0], ss = rsum[0];
         for (int w = 1; w < kDftThreads / 32; ++w) {
-            if (dbetter(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; }
+            if (dbetter(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; bc = rc[w]; }
             if (a.half_p > 0.f) {
                 float nv = fmaxf(vv, rv[w]);
                 float sa = (vv > 0.f) ? ss * exp2f(a.half_p * __log2f(vv / nv)) : 0.f;
@@ -197,6 +202,7 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
         }
         a.pkey[bx] = b;
         a.pidx[bx] = (b >= (K)0) ? bi : -1;
+        if (a.pchi) a.pchi[bx] = bc;
         if (a.pvmax) { a.pvmax[bx] = vv; a.psum[bx] = ss; }
     }
 }

@@ -117,6 +117,7 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
 
     K best = (K)-1;
     int best_li = 0;                          // (d - d_begin) * L + bin
+    C best_c = zero;                          // chi at that cell
     float pv = 0.f, ps = 0.f;                 // p-norm partials (key domain)
 
     for (int d0 = d_begin; d0 < d_end; d0 += RS) {
@@ -164,7 +165,7 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                         const float w = __ldg(wrow + off);
                         key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
                     }
-                    if (key > best) { best = key; best_li = lbase + off; }
+                    if (key > best) { best = key; best_li = lbase + off; best_c = c; }
                     if constexpr (MODE == MODE_REDUCE_PNORM) {
                         if (key >= (K)0) pnorm_add(a.half_p, (float)key, pv, ps);
                     }
@@ -180,7 +181,9 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
         for (int o = 16; o > 0; o >>= 1) {
             const K ob = __shfl_xor_sync(0xffffffffu, best, o);
             const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
-            if (better(ob, oi, best, best_idx)) { best = ob; best_idx = oi; }
+            const T ocx = __shfl_xor_sync(0xffffffffu, best_c.x, o);
+            const T ocy = __shfl_xor_sync(0xffffffffu, best_c.y, o);
+            if (better(ob, oi, best, best_idx)) { best = ob; best_idx = oi; best_c = mk(ocx, ocy); }
             if constexpr (MODE == MODE_REDUCE_PNORM) {
                 const float ov = __shfl_xor_sync(0xffffffffu, pv, o);
                 const float os = __shfl_xor_sync(0xffffffffu, ps, o);
@@ -189,26 +192,32 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
         }
         __shared__ K rk[kThreads / 32];
         __shared__ long long ri[kThreads / 32];
+        __shared__ C rc[kThreads / 32];
         __shared__ float rv[kThreads / 32], rsum[kThreads / 32];
         const int warp = tid >> 5;
-        if ((tid & 31) == 0) { rk[warp] = best; ri[warp] = best_idx; rv[warp] = pv; rsum[warp] = ps; }
+        if ((tid & 31) == 0) { rk[warp] = best; ri[warp] = best_idx; rc[warp] = best_c; rv[warp] = pv; rsum[warp] = ps; }
         __syncthreads();
         if (tid == 0) {
             K b = rk[0];
             long long bi = ri[0];
+            C bc = rc[0];
             float vv = rv[0], ss = rsum[0];
             for (int w = 1; w < kThreads / 32; ++w) {
-                if (better(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; }
+                if (better(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; bc = rc[w]; }
                 if constexpr (MODE == MODE_REDUCE_PNORM) pnorm_merge(a.half_p, vv, ss, rv[w], rsum[w]);
             }
             a.pkey[blockIdx.x] = b;
             a.pidx[blockIdx.x] = (b >= (K)0) ? bi : -1;
+            if (a.pchi) a.pchi[blockIdx.x] = bc;
             if (a.pvmax) { a.pvmax[blockIdx.x] = vv; a.psum[blockIdx.x] = ss; }
         }
     }
 }
 
 // ------------------------------------------------------------------ host ----
+// A row needs L/E <= 256 threads (one CTA), so L = 4096 always takes E = 16.
+static bool elems_ok(int L, int E) { return (E == 8 || E == 16) && L >= 2 * E && L / E <= kThreads; }
+
 template <int L, int E, typename C>
 static int smem_for(int N) {
     using PL = Plan<L, E>;
@@ -256,13 +265,42 @@ static cudaError_t launch_any(const FwdArgs<C, K>& a, cudaStream_t s, bool prepa
         case 512: return e8 ? launch_LE<512, 8>(a, s, prepare_only) : launch_LE<512, 16>(a, s, prepare_only);
         case 1024: return e8 ? launch_LE<1024, 8>(a, s, prepare_only) : launch_LE<1024, 16>(a, s, prepare_only);
         case 2048: return e8 ? launch_LE<2048, 8>(a, s, prepare_only) : launch_LE<2048, 16>(a, s, prepare_only);
-        case 4096: return e8 ? launch_LE<4096, 8>(a, s, prepare_only) : launch_LE<4096, 16>(a, s, prepare_only);
+        case 4096: return e8 ? cudaErrorInvalidValue : launch_LE<4096, 16>(a, s, prepare_only);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s) { return launch_any(a, s, false); }
 cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s) { return launch_any(a, s, false); }
+
+template <int L, int E, typename C, typename K>
+static int occupancy_LE(int N) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_fft_kernel<L, E, MODE_REDUCE, C, K>, kThreads,
+                                                      smem_for<L, E, C>(N)) != cudaSuccess)
+        return 1;
+    return occ > 0 ? occ : 1;
+}
+
+template <typename C, typename K>
+static int occupancy_any(int L, int N, int E) {
+    const bool e8 = (E == 8);
+    switch (L) {
+        case 32: return e8 ? occupancy_LE<32, 8, C, K>(N) : occupancy_LE<32, 16, C, K>(N);
+        case 64: return e8 ? occupancy_LE<64, 8, C, K>(N) : occupancy_LE<64, 16, C, K>(N);
+        case 128: return e8 ? occupancy_LE<128, 8, C, K>(N) : occupancy_LE<128, 16, C, K>(N);
+        case 256: return e8 ? occupancy_LE<256, 8, C, K>(N) : occupancy_LE<256, 16, C, K>(N);
+        case 512: return e8 ? occupancy_LE<512, 8, C, K>(N) : occupancy_LE<512, 16, C, K>(N);
+        case 1024: return e8 ? occupancy_LE<1024, 8, C, K>(N) : occupancy_LE<1024, 16, C, K>(N);
+        case 2048: return e8 ? occupancy_LE<2048, 8, C, K>(N) : occupancy_LE<2048, 16, C, K>(N);
+        case 4096: return occupancy_LE<4096, 16, C, K>(N);
+        default: return 1;
+    }
+}
+
+int fft_occupancy(int L, int N, int E, bool fp64) {
+    return fp64 ? occupancy_any<double2, double>(L, N, E) : occupancy_any<float2, float>(L, N, E);
+}
 
 cudaError_t fft_prepare_f32(int L, int N, int E) {
     FwdArgs<float2, float> a{};
@@ -277,6 +315,7 @@ cudaError_t fft_prepare_f64(int L, int N, int E) {
 
 template <typename C, int E>
 static int smem_any(int L, int N) {
+    if (!elems_ok(L, E)) return -1;
     switch (L) {
         case 32: return smem_for<32, E, C>(N);
         case 64: return smem_for<64, E, C>(N);
@@ -295,15 +334,15 @@ int fft_smem_bytes(int L, int N, bool fp64, int E) {
     return fp64 ? smem_any<double2, 16>(L, N) : smem_any<float2, 16>(L, N);
 }
 
-int fft_rows_per_cta(int L, int E) { return (L >= 2 * E && L <= 4096) ? kThreads / (L / E) : 0; }
+int fft_rows_per_cta(int L, int E) { return elems_ok(L, E) ? kThreads / (L / E) : 0; }
 
 int fft_default_elems(int L, bool fp64) {
     if (const char* e = getenv("SQNGD_FFT_E")) {
         const int v = atoi(e);
-        if ((v == 8 || v == 16) && L >= 2 * v) return v;
+        if (elems_ok(L, v)) return v;
     }
-    if (fp64) return 8;
-    return (L >= 512) ? 8 : 16;
+    if (fp64) return elems_ok(L, 8) ? 8 : 16;
+    return 16;
 }
 
 }  // namespace af

@@ -42,13 +42,18 @@ struct FwdArgs {
     C* chi_out;            // FWD_DUMP output
     long long* ctr_inc;    // if set, CTA 0 adds 1 to ctr_inc[0] (outer-iteration counter)
     int fft_e;             // FFT path: values per thread (8 or 16); selects the twiddle plan
+    C* pchi;               // [grid] chi at each CTA's best cell (may be nullptr)
 };
+
+// Strips (CTAs) per waveform row of the finish kernel.
+int fin_strips(int N);
 
 // FFT path with E values per thread: dynamic shared memory bytes (-1 if L
 // unsupported), row slots per 256-thread CTA, and the default E for L.
 int fft_smem_bytes(int L, int N, bool fp64, int E);
 int fft_rows_per_cta(int L, int E);
 int fft_default_elems(int L, bool fp64);
+int fft_occupancy(int L, int N, int E, bool fp64);   // resident CTAs per SM (reduce kernel)
 cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
 cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
 cudaError_t fft_prepare_f32(int L, int N, int E);

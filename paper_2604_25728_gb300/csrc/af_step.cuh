@@ -32,6 +32,7 @@ struct FinArgs {
     const long long* pidx;
     const float* pvmax;
     const float* psum;
+    const float2* pchi;       // [nblk] chi at each forward CTA's best cell
     const double2* cdiag;     // [M]
     int weight_mode;          // WeightMode
     float w0;
@@ -79,6 +80,10 @@ struct FinArgs {
     float2* best_h;
     double snrl_db;
     double p_accept2;         // (10^{-(snrl_db + 0.05)/20})^2: a design is acceptable when min p_m^2 >= this
+    // projection across the CTAs of one row (FIN_ADAM_H): partial ||h||^2 per
+    // strip, and a per-row arrival counter (zero between launches)
+    double* norm_part;        // [M][strips]
+    unsigned int* row_ctr;    // [M]
 };
 
 struct AccArgs {

@@ -80,6 +80,9 @@ struct af_ctx {
     long long* pidx = nullptr;
     float* pvmax = nullptr;
     float* psum = nullptr;
+    float2* pchi = nullptr;    // [nblk] chi at each forward CTA's best cell
+    double* norm_part = nullptr;   // [M][strips] partial filter energies
+    unsigned int* row_ctr = nullptr;  // [M] arrival counters of the finish kernel
     double* pkey64 = nullptr;
     long long* pidx64 = nullptr;
     double2* cdiag = nullptr;
@@ -156,13 +159,33 @@ static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
                     c->xs, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
-                    c->ctr, c->best2, c->log};
+                    c->ctr, c->best2, c->log, c->pchi, c->norm_part, c->row_ctr};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
+}
+
+// Rows per CTA for the FFT forward pass: every (pair, delay) row costs the
+// same, a CTA takes RS rows per iteration, and `slots` CTAs are resident at
+// once.  Choose the iteration count per CTA that minimises
+// waves x (iterations + 1/2), the half iteration standing for the CTA's
+// prologue (loading x, h and the twiddles).
+static int pick_row_iters(int P, int D, int RS, int slots) {
+    if (slots < 1) slots = 1;
+    int best_it = 1;
+    double best_cost = 1e300;
+    const int max_it = (D + RS - 1) / RS;
+    for (int it = 1; it <= max_it; ++it) {
+        const long long rows = (long long)it * RS;
+        const long long ctas = (long long)P * ((D + rows - 1) / rows);
+        const long long waves = (ctas + slots - 1) / slots;
+        const double cost = (double)waves * (it + 0.5);
+        if (cost < best_cost) { best_cost = cost; best_it = it; }
+    }
+    return best_it;
 }
 
 static af_status validate(const af_config* g, std::string* why) {
@@ -278,12 +301,13 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     if ((s = upload(c, &c->pre, pre)) || (s = upload(c, &c->pre64, pre64)) || (s = upload(c, &c->wL, wL)) ||
         (s = upload(c, &c->level, lev)) || (s = upload(c, &c->level64, lev64)))
         return fail(s);
-    // Stockham twiddles: for every pass p >= 1 a table [R][NS] of e^{+j 2 pi r k / (NS R)}
+    // Stockham twiddles: for every pass p >= 1 a table [R-1][NS] of
+    // e^{+j 2 pi r k / (NS R)}, r = 1..R-1 (the r = 0 row is all ones)
     auto twiddles = [&](int E, std::vector<double2>& out) {
         const auto plan = fft_plan(L, E);
         for (size_t p = 1; p < plan.size(); ++p) {
             const int R = plan[p].R, NS = plan[p].NS;
-            for (int r = 0; r < R; ++r)
+            for (int r = 1; r < R; ++r)
                 for (int k = 0; k < NS; ++k) {
                     double re, im;
                     phasor((double)r * k / ((double)NS * R), &re, &im);
@@ -331,10 +355,11 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     }
 
     // ---- launch geometry and workspace ----
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
     if (c->path == AF_PATH_FFT) {
         const int RS = fft_rows_per_cta(L, c->fft_e);
-        int it = (int)lround((double)c->P * c->D / ((double)RS * 152 * 6));
-        if (it < 1) it = 1;
+        int it = pick_row_iters(c->P, c->D, RS, sms * fft_occupancy(L, N, c->fft_e, false));
         if (const char* e = getenv("SQNGD_FFT_ROW_ITERS")) it = atoi(e) > 0 ? atoi(e) : it;
         c->rows_per_chunk = RS * it;
         c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
@@ -347,8 +372,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     c->nblk = c->P * c->ctas_per_pair;
     if (c->acc_fft) {
         const int RS = fft_rows_per_cta(L, c->acc_e);
-        int it = (c->P * c->D) / (RS * 152 * 4);
-        if (it < 1) it = 1;
+        const int it = pick_row_iters(c->P, c->D, RS, sms * fft_occupancy(L, N, c->acc_e, true));
         c->acc_rows_per_chunk = RS * it;
         c->acc_n_chunks = (c->D + c->acc_rows_per_chunk - 1) / c->acc_rows_per_chunk;
         c->acc_ctas_per_pair = c->acc_n_chunks;
@@ -361,13 +385,19 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     const size_t MN = (size_t)M * N;
     if ((s = dalloc(c, &c->pkey, c->nblk)) || (s = dalloc(c, &c->pidx, c->nblk)) ||
         (s = dalloc(c, &c->pvmax, c->nblk)) || (s = dalloc(c, &c->psum, c->nblk)) ||
+        (s = dalloc(c, &c->pchi, c->nblk)) || (s = dalloc(c, &c->norm_part, (size_t)M * fin_strips(N))) ||
+        (s = dalloc(c, &c->row_ctr, M)) ||
         (s = dalloc(c, &c->pkey64, c->acc_nblk)) || (s = dalloc(c, &c->pidx64, c->acc_nblk)) ||
         (s = dalloc(c, &c->cdiag, M)) || (s = dalloc(c, &c->xs, MN)) || (s = dalloc(c, &c->dydz, MN)) ||
         (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
         (s = dalloc(c, &c->acc_out, 4 + M)) || (s = dalloc(c, &c->terms_scratch, AF_TERMS_FIXED + M)) ||
         (s = dalloc(c, &c->errflag, 1)) || (s = dalloc(c, &c->ctr, 4)) || (s = dalloc(c, &c->best2, 8)))
         return fail(s);
-    if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) { c->err = "cudaMemset failed"; return fail(AF_ERR_CUDA); }
+    if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->row_ctr, 0, sizeof(unsigned int) * M) != cudaSuccess) {
+        c->err = "cudaMemset failed";
+        return fail(AF_ERR_CUDA);
+    }
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
@@ -427,7 +457,7 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
     a.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM;
     a.mode = FWD_REDUCE;
     a.half_p = (float)(c->cfg.pnorm * 0.5);
-    a.pkey = c->pkey; a.pidx = c->pidx; a.pvmax = c->pvmax; a.psum = c->psum;
+    a.pkey = c->pkey; a.pidx = c->pidx; a.pvmax = c->pvmax; a.psum = c->psum; a.pchi = c->pchi;
     a.cdiag = c->cdiag;
     a.fft_e = c->fft_e;
     return a;
@@ -441,7 +471,8 @@ static FinArgs fin_args(af_ctx* c) {
     FinArgs f{};
     f.M = c->cfg.M; f.N = c->cfg.N; f.L = c->cfg.L; f.D = c->D; f.k_lo = c->cfg.k_lo;
     f.nblk = c->nblk; f.ctas_per_pair = c->ctas_per_pair;
-    f.pkey = c->pkey; f.pidx = c->pidx; f.pvmax = c->pvmax; f.psum = c->psum;
+    f.pkey = c->pkey; f.pidx = c->pidx; f.pvmax = c->pvmax; f.psum = c->psum; f.pchi = c->pchi;
+    f.norm_part = c->norm_part; f.row_ctr = c->row_ctr;
     f.cdiag = c->cdiag;
     f.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM;
     f.w0 = c->w0; f.wmap = c->wmap;
