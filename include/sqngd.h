@@ -234,6 +234,34 @@ AF_API af_status sqngd_step(af_ctx* ctx, af_state* st, int32_t n_outer, double* 
  */
 AF_API af_status af_eval_hard(af_ctx* ctx, const float* u_dev, const float* h_dev, double* out_host);
 
+/*
+ * Loss terms without any device allocation.  The paper has no counterpart:
+ * this is a service entry point for callers that cannot call cudaMalloc --
+ * code running while a stream is captured into a CUDA graph, hosts whose
+ * framework owns the device memory pool and forbids raw allocations, and
+ * latency-critical loops that cannot afford an allocation's implicit
+ * synchronisation.  It needs no context.
+ *
+ * Computes the same terms record as af_loss_grad_xh (terms_dev: device
+ * [AF_TERMS_FIXED + M] doubles) for waveforms x_dev and filters h_dev
+ * (complex [M][N], device) on the uniform Doppler grid nu_j = nu0 + j/L
+ * (cycles/chip), delays k_lo..k_hi, weight 1/N on every cell, loss constants
+ * eps and snrl_db; no gradient.  Enqueued on `stream` (a cudaStream_t).
+ *
+ * All scratch lives in one file-scope device array of about 0.3 MB that
+ * every GPU loading the library keeps until exit.  Limits: M <= 16,
+ * N <= 4096, L a power of two in 32..4096, and the forward pass must fit in
+ * shared memory; anything else returns AF_ERR_INVALID_ARG before any launch.
+ * The first call on a device looks the array up (cudaGetSymbolAddress):
+ * make it before any stream capture.  Calls share the array, so calls that
+ * overlap on the GPU race; every call rewrites the scratch it reads, so
+ * nothing needs clearing between calls.  Returns AF_ERR_CUDA if a lookup or
+ * launch fails.
+ */
+AF_API af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, double nu0, int32_t k_lo, int32_t k_hi,
+                                       double eps, double snrl_db, const float* x_dev, const float* h_dev,
+                                       double* terms_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,8 @@ SIGNATURES = {
     "sqngd_init": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sqngd_step": (c_int32, [c_void_p, ctypes.POINTER(AfState), c_int32, P_double]),
     "af_eval_hard": (c_int32, [c_void_p, c_void_p, c_void_p, P_double]),
+    "af_loss_terms_noalloc": (c_int32, [c_int32, c_int32, c_int32, c_double, c_int32, c_int32, c_double, c_double,
+                                        c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lock = threading.Lock()
