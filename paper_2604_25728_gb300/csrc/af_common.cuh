@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace af {
 
 // ---------------------------------------------------------------- complex --
@@ -221,5 +223,32 @@ inline cudaError_t set_smem_once(const void* func, int bytes) {
         if (table[i].f == func && table[i].dev == dev) { table[i].bytes = bytes; return cudaSuccess; }
     if (n < 256) table[n++] = Entry{func, dev, bytes};
     return cudaSuccess;
+}
+}  // namespace af
+
+namespace af {
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may start before the kernel ahead of it in
+// the stream has finished; pdl_wait() blocks until that kernel has completed
+// and its memory is visible (a no-op when there is no such dependency), and
+// pdl_trigger() lets the next kernel in the stream start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch `kern` with optional programmatic stream serialisation.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 }  // namespace af

@@ -32,6 +32,8 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
     C* Bs = As + NK * TR;          // [NK][TC]
 
     const int tid = threadIdx.x;
+    pdl_wait();
+    pdl_trigger();
     if (a.ctr_inc != nullptr && blockIdx.x == 0 && tid == 0) a.ctr_inc[0] += 1;
     const int n_ctiles = (a.L + TC - 1) / TC;
     const int bx = blockIdx.x;
@@ -215,8 +217,7 @@ static cudaError_t launch_dft(const FwdArgs<C, K>& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int n_ctiles = (a.L + TC - 1) / TC;
     const int grid = a.M * a.M * a.n_chunks * n_ctiles;
-    kern<<<grid, kDftThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(kern, dim3(grid), dim3(kDftThreads), smem, s, a.pdl != 0, a);
 }
 
 template <typename C, typename K>

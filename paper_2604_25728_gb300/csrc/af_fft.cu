@@ -70,10 +70,16 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     C* bufs = tws + PL::tw_len;               // [RS][padlen]
 
     const int tid = threadIdx.x;
-    if (a.ctr_inc != nullptr && blockIdx.x == 0 && tid == 0) a.ctr_inc[0] += 1;
     const int pair = blockIdx.x / a.n_chunks;
     const int chunk = blockIdx.x - pair * a.n_chunks;
     const int m = pair / a.M, l = pair - m * a.M;
+
+    // Constant tables first: with programmatic launch this overlaps the tail
+    // of the kernel that produces x and h.
+    for (int i = tid; i < PL::tw_len; i += kThreads) tws[i] = a.tw[i];
+    pdl_wait();
+    pdl_trigger();
+    if (a.ctr_inc != nullptr && blockIdx.x == 0 && tid == 0) a.ctr_inc[0] += 1;
 
     const C zero = mk((T)0, (T)0);
     for (int n = tid; n < XS; n += kThreads) xs[n] = (n < N) ? cmul(a.x[(size_t)m * N + n], a.pre[n]) : zero;
@@ -81,7 +87,6 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
         const int p = i - N;
         hp[i] = (p >= 0 && p < N) ? a.h[(size_t)l * N + p] : zero;
     }
-    for (int i = tid; i < PL::tw_len; i += kThreads) tws[i] = a.tw[i];
 
     // chi_mm(0, 0) = h_m^H x_m in FP64 (Eq. 38), once per waveform.
     if (a.cdiag != nullptr && m == l && chunk == 0) {
@@ -232,8 +237,7 @@ static cudaError_t launch_LEM(const FwdArgs<C, K>& a, cudaStream_t s, bool prepa
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess || prepare_only) return e;
     const int grid = a.M * a.M * a.n_chunks;
-    kern<<<grid, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(kern, dim3(grid), dim3(kThreads), smem, s, a.pdl != 0, a);
 }
 
 template <int L, int E, typename C, typename K>

@@ -17,6 +17,10 @@
 // the last CTA of the row to arrive (atomic counter, no waiting) sums the
 // partials in a fixed order and rescales the row.  A CTA reads other
 // elements of a row only in modes that write nothing.
+//
+// Programmatic launch: the kernel may start while the forward pass is still
+// running.  Before pdl_wait() it only reads its own element's inputs, which
+// the forward pass does not write; every global write comes after it.
 #include <math.h>
 
 #include "af_common.cuh"
@@ -33,11 +37,21 @@ __device__ __forceinline__ float2 cell_phasor(const FinArgs& a, int j, int n) {
     return a.E[(size_t)n * a.L + j];
 }
 
+// sqrt of a non-negative double: FP32 square root refined by one Newton step
+// (relative error ~1e-15), avoiding the long FP64 square-root sequence.
+__device__ __forceinline__ double sqrt_d(double v) {
+    if (!(v > 0.0)) return 0.0;
+    const float s = sqrtf((float)v);
+    const double r = (double)s;
+    return r + (double)((float)fma(-r, r, v) / (2.f * s));
+}
+
 __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
     const int m = blockIdx.y;
     const int strip = blockIdx.x;
     const int S = gridDim.x;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int M = a.M, N = a.N;
     const int n = strip * kFT + tid;
     const bool in = n < N;
@@ -49,6 +63,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
     __shared__ float2 sc2[2][kFT / 32];
     __shared__ float spv[2][kFT / 32], sps[2][kFT / 32];
     __shared__ double s_terms[8];
+    __shared__ double s_pmin2;
     __shared__ float2 s_g;           // sparse coefficient g
     __shared__ int s_cell[4];        // m*, l*, k*, j*  (m* = -1: no sparse term)
     __shared__ float2 s_G;           // SNRL coefficient of row m
@@ -56,7 +71,9 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
     __shared__ int s_ok, s_last;
     __shared__ float s_scale;
 
-    // ---- 0. this element's inputs (independent of the forward pass) ------------
+    pdl_trigger();
+
+    // ---- 0. this element's inputs (not written by the forward pass) ----------
     const float2 zero2 = make_float2(0.f, 0.f);
     float2 xm = zero2, hm = zero2, mh = zero2, vh = zero2;
     float uu = 0.f, mu = 0.f, vu = 0.f, dy = 0.f;
@@ -67,6 +84,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
         if (a.mode == FIN_ADAM_U) { uu = a.u[e]; mu = a.m_u[e]; vu = a.v_u[e]; dy = a.dydz[e]; }
         if (a.mode == FIN_GRAD_U && a.grad_u != nullptr) { uu = a.u[e]; dy = a.dydz[e]; }
     }
+    pdl_wait();
 
     // ---- 1. merge the forward partials per class ------------------------------
     float kb[2] = {-1.f, -1.f};
@@ -109,12 +127,43 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
             const float os = __shfl_xor_sync(0xffffffffu, ps[c], o);
             if (a.half_p > 0.f) pmerge(a.half_p, pv[c], ps[c], ov, os);
         }
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             sk[c][tid >> 5] = kb[c]; si[c][tid >> 5] = ib[c]; sc2[c][tid >> 5] = cb[c];
             spv[c][tid >> 5] = pv[c]; sps[c][tid >> 5] = ps[c];
         }
     }
+
+    // ---- 2. SNRL term, one waveform per lane of warp 0 (FP64) -----------------
+    if (tid < 32) {
+        double p = 0.0, c2 = 0.0;
+        double2 cm = make_double2(0.0, 0.0);
+        if (lane < M) {
+            cm = a.cdiag[lane];
+            c2 = cm.x * cm.x + cm.y * cm.y;
+            p = sqrt_d(c2) * a.inv_N;                      // p_m = |A_mm(0,0)| / N (Eq. 38)
+        }
+        const double dev = p - a.ptar;
+        double ls = (lane < M) ? dev * dev : 0.0;
+        double pmin2 = (lane < M) ? c2 * a.inv_N * a.inv_N : 1e300;
+        for (int o = 16; o > 0; o >>= 1) {
+            ls += __shfl_xor_sync(0xffffffffu, ls, o);
+            pmin2 = fmin(pmin2, __shfl_xor_sync(0xffffffffu, pmin2, o));
+        }
+        if (lane == m) {
+            // G_m = (1-eps)(2/M)(p_m - p_tar)/N * c_m/|c_m|
+            const float mag = (float)(p * (double)N);
+            const float coef = (mag > 0.f) ? (float)((1.0 - a.eps) * (2.0 / M) * dev * a.inv_N) / mag : 0.f;
+            s_G = make_float2(coef * (float)cm.x, coef * (float)cm.y);
+        }
+        if (lane == 0) {
+            s_terms[4] = ls / (double)M;                   // L_SNRL (Eq. 41)
+            s_pmin2 = pmin2;
+        }
+        if (m == 0 && strip == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = p;
+    }
     __syncthreads();
+
+    // ---- 3. class values, loss, winning cell ---------------------------------
     if (tid == 0) {
         double cv[2];
         long long cell[2];
@@ -133,24 +182,18 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
             cell[c] = any ? i : -1;
             chi[c] = x;
             if (!any) cv[c] = 0.0;
-            else if (a.half_p > 0.f) cv[c] = wscale * sqrt((double)v) * pow((double)s, 0.5 / (double)a.half_p);
+            else if (a.half_p > 0.f) cv[c] = wscale * (double)(sqrtf(v) * powf(s, 0.5f / a.half_p));
             else cv[c] = wscale * (double)sqrtf(k);
         }
         const int cls = (cv[0] >= cv[1]) ? 0 : 1;
         const double lw = cv[cls];
-        double ls = 0.0;
-        for (int mm = 0; mm < M; ++mm) {
-            const double2 c = a.cdiag[mm];
-            const double p = sqrt(c.x * c.x + c.y * c.y) / (double)N;
-            ls += (p - a.ptar) * (p - a.ptar);
-        }
-        ls /= (double)M;
-        s_terms[0] = a.eps * lw + (1.0 - a.eps) * ls;
-        s_terms[1] = lw; s_terms[2] = cv[0]; s_terms[3] = cv[1]; s_terms[4] = ls;
+        const double ls = s_terms[4];
+        s_terms[0] = a.eps * lw + (1.0 - a.eps) * ls;      // Eq. 42
+        s_terms[1] = lw; s_terms[2] = cv[0]; s_terms[3] = cv[1];
         s_terms[5] = (double)cls; s_terms[6] = (double)cell[0]; s_terms[7] = (double)cell[1];
         // winning cell of the exact max and its coefficient g = eps w chi/|chi|
         s_cell[0] = -1;
-        s_g = make_float2(0.f, 0.f);
+        s_g = zero2;
         if (a.half_p <= 0.f && cell[cls] >= 0) {
             const long long cc = cell[cls];
             int j, d, pair;
@@ -166,29 +209,16 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
                 pair = (int)(cc / ((long long)a.L * a.D));
             }
             s_cell[0] = pair / M; s_cell[1] = pair % M; s_cell[2] = a.k_lo + d; s_cell[3] = j;
-            const double cr = chi[cls].x, ci = chi[cls].y;
-            const double mag = sqrt(cr * cr + ci * ci);
-            const double w = (a.weight_mode == WM_UNIFORM) ? (double)a.w0 : (double)a.wmap[(size_t)d * a.L + j];
-            if (mag > 0.0) s_g = make_float2((float)(a.eps * w * cr / mag), (float)(a.eps * w * ci / mag));
-        }
-        // SNRL coefficient G_m = (1-eps)(2/M)(p_m - p_tar)/N * c_m/|c_m|
-        {
-            const double2 c = a.cdiag[m];
-            const double mag = sqrt(c.x * c.x + c.y * c.y);
-            s_G = make_float2(0.f, 0.f);
-            if (mag > 0.0) {
-                const double coef = (1.0 - a.eps) * (2.0 / M) * (mag / N - a.ptar) / N / mag;
-                s_G = make_float2((float)(coef * c.x), (float)(coef * c.y));
+            const float cr = chi[cls].x, ci = chi[cls].y;
+            const float mag = sqrtf(cr * cr + ci * ci);
+            const float w = (a.weight_mode == WM_UNIFORM) ? a.w0 : a.wmap[(size_t)d * a.L + j];
+            if (mag > 0.f) {
+                const float f = (float)a.eps * w / mag;
+                s_g = make_float2(f * cr, f * ci);
             }
         }
         if (m == 0 && strip == 0) {
-            if (a.terms) {
-                for (int i = 0; i < 8; ++i) a.terms[i] = s_terms[i];
-                for (int mm = 0; mm < M; ++mm) {
-                    const double2 c = a.cdiag[mm];
-                    a.terms[8 + mm] = sqrt(c.x * c.x + c.y * c.y) / (double)N;
-                }
-            }
+            if (a.terms) for (int i = 0; i < 8; ++i) a.terms[i] = s_terms[i];
             if (a.log) {
                 const long long o = a.ctr ? a.ctr[0] - 1 : 0;
                 double* lg = a.log + ((size_t)o * a.evals_per_outer + a.eval_index) * 4;
@@ -204,7 +234,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
     const int ms = s_cell[0], ls_ = s_cell[1], ks = s_cell[2], js = s_cell[3];
     const float2 g = s_g, Gm = s_G;
 
-    // ---- 2. this thread's element of row m of the gradient ---------------------
+    // ---- 4. this thread's element of row m of the gradient ---------------------
     float2 gx = zero2, gh = zero2;
     if (in) {
         if (need_gx) {
@@ -230,7 +260,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
         }
     }
 
-    // ---- 3. outputs ---------------------------------------------------------------
+    // ---- 5. outputs ---------------------------------------------------------------
     if (a.mode == FIN_GRAD_XH || a.mode == FIN_GRAD_U) {
         if (!in) return;
         bool bad = !isfinite(gx.x) || !isfinite(gx.y) || !isfinite(gh.x) || !isfinite(gh.y);
@@ -255,38 +285,30 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
         // 1 - beta^t = -expm1(t ln beta), FP32 (relative error ~1e-6 at any t)
         s_adam[0] = -expm1f((float)t * log1pf(a.b1 - 1.f));
         s_adam[1] = -expm1f((float)t * log1pf(a.b2 - 1.f));
+        if (a.mode == FIN_ADAM_H && a.snap_best) {
+            // best-design record: this evaluation scored the hard design (X_hard, H)
+            const double* prev = a.best2 + ((o + 1) & 1) * 4;
+            double* cur = a.best2 + (o & 1) * 4;
+            // SNRL_m = -20 log10 p_m <= target + 0.05 dB  <=>  p_m^2 >= p_accept2
+            s_ok = (s_pmin2 >= a.p_accept2 && s_terms[1] < prev[0]) ? 1 : 0;
+            if (m == 0 && strip == 0) {
+                if (s_ok) {
+                    cur[0] = s_terms[1]; cur[1] = s_terms[0];
+                    cur[2] = (double)(a.ctr[3] + o); cur[3] = -10.0 * log10(s_pmin2);
+                } else {
+                    for (int i = 0; i < 4; ++i) cur[i] = prev[i];
+                }
+            }
+        }
     }
     __syncthreads();
     const float c1 = s_adam[0], c2 = s_adam[1];
     bool bad = false;
 
     if (a.mode == FIN_ADAM_H) {
-        // best-design record: this evaluation scored the hard design (X_hard, H)
-        if (a.snap_best) {
-            const double* prev = a.best2 + ((o + 1) & 1) * 4;
-            double* cur = a.best2 + (o & 1) * 4;
-            // SNRL_m = -20 log10 p_m <= target + 0.05 dB  <=>  p_m^2 >= p_accept2
-            if (tid == 0) {
-                double pmin2 = 1e300;
-                for (int mm = 0; mm < M; ++mm) {
-                    const double2 c = a.cdiag[mm];
-                    pmin2 = fmin(pmin2, (c.x * c.x + c.y * c.y) / ((double)N * N));
-                }
-                s_ok = (pmin2 >= a.p_accept2 && s_terms[1] < prev[0]) ? 1 : 0;
-                if (m == 0 && strip == 0) {
-                    if (s_ok) {
-                        cur[0] = s_terms[1]; cur[1] = s_terms[0];
-                        cur[2] = (double)(a.ctr[3] + o); cur[3] = -10.0 * log10(pmin2);
-                    } else {
-                        for (int i = 0; i < 4; ++i) cur[i] = prev[i];
-                    }
-                }
-            }
-            __syncthreads();
-            if (s_ok && in) {
-                if (a.best_h) a.best_h[e] = hm;
-                if (a.best_q) a.best_q[e] = hard_q(a.qa, sigmoidf_(uu));
-            }
+        if (a.snap_best && s_ok && in) {
+            if (a.best_h) a.best_h[e] = hm;
+            if (a.best_q) a.best_q[e] = hard_q(a.qa, sigmoidf_(uu));
         }
         // Adam on (H_Re, H_Im) of this element, then the projection of Eq. 32
         double e2 = 0.0;
@@ -318,7 +340,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
             if (tid == 0) {
                 double tot = 0.0;
                 for (int s = 0; s < S; ++s) tot += __ldcg(a.norm_part + (size_t)m * S + s);
-                s_scale = (tot > 0.0) ? (float)sqrt((double)N / tot) : 1.f;
+                s_scale = (tot > 0.0) ? (float)sqrt_d((double)N / tot) : 1.f;
                 a.row_ctr[m] = 0u;
                 if (!isfinite(s_scale) && a.err_flag) atomicExch(a.err_flag, 1);
             }
@@ -362,9 +384,8 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
 int fin_strips(int N) { return (N + kFT - 1) / kFT; }
 
 cudaError_t launch_fin(const FinArgs& a, cudaStream_t s) {
-    dim3 grid(fin_strips(a.N), a.M);
-    fin_kernel<<<grid, kFT, 0, s>>>(a);
-    return cudaGetLastError();
+    const dim3 grid(fin_strips(a.N), a.M);
+    return launch_ex(fin_kernel, grid, dim3(kFT), 0, s, a.pdl != 0, a);
 }
 
 }  // namespace af

@@ -43,6 +43,7 @@ struct FwdArgs {
     long long* ctr_inc;    // if set, CTA 0 adds 1 to ctr_inc[0] (outer-iteration counter)
     int fft_e;             // FFT path: values per thread (8 or 16); selects the twiddle plan
     C* pchi;               // [grid] chi at each CTA's best cell (may be nullptr)
+    int pdl;               // launch with programmatic stream serialisation
 };
 
 // Strips (CTAs) per waveform row of the finish kernel.

@@ -38,6 +38,8 @@ struct FinArgs {
     float w0;
     const float* wmap;        // [D][L]
     double eps, ptar;
+    double inv_N;             // 1/N
+    int pdl;                  // launch with programmatic stream serialisation
     float half_p;             // p/2 (0 = exact max)
     int grid_fft;             // 1: nu_j = nu_0 + j/L (phasor = pre(n) wL[(j n) mod L]); 0: table E
     const float2* pre;        // [N]

@@ -74,6 +74,7 @@ struct af_ctx {
     int n_chunks = 0, rows_per_chunk = 0, nblk = 0, ctas_per_pair = 0;
     bool acc_fft = false;
     bool rho_uniform = true;   // thresholds are the default (i + 1/2)/K
+    bool pdl = true;           // programmatic dependent launch between forward and finish kernels
     int fft_e = 0, acc_e = 0;  // FFT values per thread: FP32 path, FP64 acceptance
     int acc_n_chunks = 0, acc_rows_per_chunk = 0, acc_nblk = 0, acc_ctas_per_pair = 0;
     float* pkey = nullptr;
@@ -248,6 +249,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     c->K = cfg->B * cfg->r_n;
     c->w0 = (float)(1.0 / N);
     c->stream = (cudaStream_t)stream;
+    if (const char* e = getenv("SQNGD_NO_PDL")) c->pdl = (atoi(e) == 0);
     auto fail = [&](af_status s) {
         g_init_error = c->err;
         free_all(c);
@@ -460,6 +462,7 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
     a.pkey = c->pkey; a.pidx = c->pidx; a.pvmax = c->pvmax; a.psum = c->psum; a.pchi = c->pchi;
     a.cdiag = c->cdiag;
     a.fft_e = c->fft_e;
+    a.pdl = c->pdl ? 1 : 0;
     return a;
 }
 
@@ -477,6 +480,8 @@ static FinArgs fin_args(af_ctx* c) {
     f.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM;
     f.w0 = c->w0; f.wmap = c->wmap;
     f.eps = c->cfg.eps;
+    f.inv_N = 1.0 / c->cfg.N;
+    f.pdl = c->pdl ? 1 : 0;
     f.ptar = pow(10.0, -c->cfg.snrl_db / 20.0);
     f.half_p = (float)(c->cfg.pnorm * 0.5);
     f.grid_fft = c->grid_fft ? 1 : 0;
