@@ -49,6 +49,32 @@ struct FwdArgs {
 // Strips (CTAs) per waveform row of the finish kernel.
 int fin_strips(int N);
 
+// Dense adjoint of the p-norm sidelobe loss on the FFT grid (same launch
+// geometry as the forward pass).
+struct AdjArgs {
+    int M, N, L, D, k_lo;
+    int n_chunks, rows_per_chunk;
+    const float2* x;       // [M][N] waveforms of this evaluation
+    const float2* h;       // [M][N] filters
+    const float2* pre;     // [N] e^{j 2 pi nu_0 n}
+    const float2* tw;      // FFT twiddle tables
+    const float* wmap;     // [D][L] or nullptr
+    int weight_mode;
+    float w0;
+    double eps;
+    float half_p;          // p/2
+    int nblk_fwd, ctas_per_pair_fwd;
+    const float* pvmax;    // forward p-norm partials
+    const float* psum;
+    float2* part;          // [grid][2][N] per-CTA partial rows (grad x_m, grad h_l)
+    float2* dense;         // [2][M][N] summed sidelobe gradient (x, h)
+    int fft_e;
+    int pdl;
+};
+cudaError_t launch_adj(const AdjArgs& a, cudaStream_t s);
+cudaError_t adj_prepare(int L, int N, int E);
+int adj_smem_bytes(int L, int N, int E);
+
 // FFT path with E values per thread: dynamic shared memory bytes (-1 if L
 // unsupported), row slots per 256-thread CTA, and the default E for L.
 int fft_smem_bytes(int L, int N, bool fp64, int E);

@@ -82,6 +82,8 @@ struct af_ctx {
     float* pvmax = nullptr;
     float* psum = nullptr;
     float2* pchi = nullptr;    // [nblk] chi at each forward CTA's best cell
+    float2* adj_part = nullptr;    // [nblk][2][N] dense-adjoint partial rows (p-norm loss)
+    float2* dense = nullptr;       // [2][M][N] summed dense sidelobe gradient
     double* norm_part = nullptr;   // [M][strips] partial filter energies
     unsigned int* row_ctr = nullptr;  // [M] arrival counters of the finish kernel
     double* pkey64 = nullptr;
@@ -160,7 +162,7 @@ static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
                     c->xs, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
-                    c->ctr, c->best2, c->log, c->pchi, c->norm_part, c->row_ctr};
+                    c->ctr, c->best2, c->log, c->pchi, c->norm_part, c->row_ctr, c->adj_part, c->dense};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -226,10 +228,6 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     *out = nullptr;
     std::string why;
     if (validate(cfg, &why) != AF_OK) { g_init_error = why; return AF_ERR_INVALID_ARG; }
-    if (cfg->pnorm > 0.0) {
-        g_init_error = "pnorm > 0 needs the dense adjoint, which this build does not provide";
-        return AF_ERR_UNIMPLEMENTED;
-    }
     if (cfg->path == AF_PATH_SPLIT_BF16) {
         g_init_error = "AF_PATH_SPLIT_BF16 is not available in this build";
         return AF_ERR_UNIMPLEMENTED;
@@ -272,6 +270,14 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     }
     c->path = (cfg->path == AF_PATH_AUTO) ? (uniform ? AF_PATH_FFT : AF_PATH_DFT) : cfg->path;
     c->grid_fft = uniform;
+    if (cfg->pnorm > 0.0) {
+        // the dense adjoint of the p-norm loss runs on the FFT grid
+        const int adj = (c->path == AF_PATH_FFT) ? adj_smem_bytes(L, N, c->fft_e) : -1;
+        if (adj <= 0 || adj > 227 * 1024) {
+            c->err = "pnorm > 0 needs the FFT path (uniform grid) with the adjoint fitting in shared memory";
+            return fail(AF_ERR_UNIMPLEMENTED);
+        }
+    }
     // FP64 acceptance pass: FFT when it fits in shared memory
     c->acc_e = c->grid_fft ? fft_default_elems(L, true) : 0;
     {
@@ -353,6 +359,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     {
         cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e) : dft_prepare_f32(N);
         if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
+        if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
         if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
     }
 
@@ -394,6 +401,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
         (s = dalloc(c, &c->acc_out, 4 + M)) || (s = dalloc(c, &c->terms_scratch, AF_TERMS_FIXED + M)) ||
         (s = dalloc(c, &c->errflag, 1)) || (s = dalloc(c, &c->ctr, 4)) || (s = dalloc(c, &c->best2, 8)))
+        return fail(s);
+    if (cfg->pnorm > 0.0 &&
+        ((s = dalloc(c, &c->adj_part, (size_t)c->nblk * 2 * N)) || (s = dalloc(c, &c->dense, 2 * MN))))
         return fail(s);
     if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->row_ctr, 0, sizeof(unsigned int) * M) != cudaSuccess) {
@@ -470,6 +480,27 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
     return (c->path == AF_PATH_FFT) ? launch_fwd_fft_f32(a, s) : launch_fwd_dft_f32(a, s);
 }
 
+// The forward pass of one evaluation, followed for the p-norm loss by the
+// dense adjoint (whose summed gradient the finish kernel then adds).
+static cudaError_t launch_eval_forward(af_ctx* c, const float2* x, const float2* h, cudaStream_t s,
+                                       long long* ctr_inc) {
+    FwdArgs<float2, float> a = fwd_args(c, x, h);
+    a.ctr_inc = ctr_inc;
+    cudaError_t e = launch_fwd(c, a, s);
+    if (e != cudaSuccess || !(c->cfg.pnorm > 0.0)) return e;
+    AdjArgs d{};
+    d.M = c->cfg.M; d.N = c->cfg.N; d.L = c->cfg.L; d.D = c->D; d.k_lo = c->cfg.k_lo;
+    d.n_chunks = c->n_chunks; d.rows_per_chunk = c->rows_per_chunk;
+    d.x = x; d.h = h; d.pre = c->pre; d.tw = c->tw;
+    d.wmap = c->wmap; d.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM; d.w0 = c->w0;
+    d.eps = c->cfg.eps; d.half_p = (float)(c->cfg.pnorm * 0.5);
+    d.nblk_fwd = c->nblk; d.ctas_per_pair_fwd = c->ctas_per_pair;
+    d.pvmax = c->pvmax; d.psum = c->psum;
+    d.part = c->adj_part; d.dense = c->dense;
+    d.fft_e = c->fft_e; d.pdl = c->pdl ? 1 : 0;
+    return launch_adj(d, s);
+}
+
 static FinArgs fin_args(af_ctx* c) {
     FinArgs f{};
     f.M = c->cfg.M; f.N = c->cfg.N; f.L = c->cfg.L; f.D = c->D; f.k_lo = c->cfg.k_lo;
@@ -495,6 +526,7 @@ static FinArgs fin_args(af_ctx* c) {
     }
     f.n_h = c->cfg.n_h; f.n_x = c->cfg.n_x;
     f.evals_per_outer = c->cfg.n_h + c->cfg.n_x;
+    if (c->cfg.pnorm > 0.0) { f.dense_g = c->dense; f.n_dense = 1; }
     f.lr = 0.f;
     f.b1 = (float)c->cfg.beta1; f.b2 = (float)c->cfg.beta2; f.adam_eps = (float)c->cfg.adam_eps;
     return f;
@@ -522,7 +554,7 @@ extern "C" af_status af_loss_grad_xh(af_ctx* c, const float* x, const float* h, 
                                      float* gh) {
     if (!c) return AF_ERR_INVALID_ARG;
     if (!x || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_xh: x and h must not be NULL");
-    CK(c, launch_fwd(c, fwd_args(c, (const float2*)x, (const float2*)h), c->stream));
+    CK(c, launch_eval_forward(c, (const float2*)x, (const float2*)h, c->stream, nullptr));
     FinArgs f = fin_args(c);
     f.mode = FIN_GRAD_XH;
     f.x = (const float2*)x;
@@ -542,7 +574,7 @@ extern "C" af_status af_loss_grad(af_ctx* c, const float* u, const float* h, int
     QuantArgs q = quant_args(c);
     float2* x = use_hard ? c->xh : c->xs;
     CK(c, launch_wave_from_logits(u, MN, q, use_hard ? 1 : 0, x, c->dydz, nullptr, c->stream));
-    CK(c, launch_fwd(c, fwd_args(c, x, (const float2*)h), c->stream));
+    CK(c, launch_eval_forward(c, x, (const float2*)h, c->stream, nullptr));
     FinArgs f = fin_args(c);
     f.mode = use_hard ? FIN_GRAD_XH : FIN_GRAD_U;
     f.x = x;
@@ -603,9 +635,8 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
     bool first = true;
     if (nh == 0) CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 0, c->xs, c->dydz, nullptr, s));
     for (int i = 0; i < nh; ++i) {
-        FwdArgs<float2, float> a = fwd_args(c, c->xh, h);
-        if (first) { a.ctr_inc = c->ctr; first = false; }
-        CK(c, launch_fwd(c, a, s));
+        CK(c, launch_eval_forward(c, c->xh, h, s, first ? c->ctr : nullptr));
+        first = false;
         FinArgs f = fin_args(c);
         f.mode = FIN_ADAM_H;
         f.x = c->xh; f.h_in = h; f.h = h;
@@ -621,9 +652,8 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
         CK(c, launch_fin(f, s));
     }
     for (int j = 0; j < nx; ++j) {
-        FwdArgs<float2, float> a = fwd_args(c, c->xs, h);
-        if (first) { a.ctr_inc = c->ctr; first = false; }
-        CK(c, launch_fwd(c, a, s));
+        CK(c, launch_eval_forward(c, c->xs, h, s, first ? c->ctr : nullptr));
+        first = false;
         FinArgs f = fin_args(c);
         f.mode = FIN_ADAM_U;
         f.x = c->xs; f.dydz = c->dydz; f.h_in = h;
