@@ -53,7 +53,8 @@ typedef enum {
     AF_ERR_INVALID_ARG = 1,   /* bad size, range or pointer; nothing was launched */
     AF_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
     AF_ERR_NONFINITE = 3,     /* a loss or gradient came out NaN/Inf (reported by af_sync) */
-    AF_ERR_TIMEOUT = 4,       /* reserved: the library has no device-side waits */
+    AF_ERR_TIMEOUT = 4,       /* a bounded device-side pipeline wait (AF_PATH_SPLIT_BF16)
+                                 gave up; the kernel ended cleanly (reported by af_sync) */
     AF_ERR_OOM = 5,           /* workspace allocation failed */
     AF_ERR_UNIMPLEMENTED = 6  /* the requested path does not support this configuration */
 } af_status;
@@ -63,7 +64,10 @@ enum {
     AF_PATH_AUTO = 0,        /* FFT when the grid is uniform with spacing 1/L, else DFT */
     AF_PATH_FFT = 1,         /* FP32 shared-memory FFT; grid nu_j = nu_0 + j/L, L = 2^p, 32..4096 */
     AF_PATH_DFT = 2,         /* FP32 direct DFT (any grid); SIMT */
-    AF_PATH_SPLIT_BF16 = 3   /* BF16 hi/lo split DFT on tcgen05 tensor cores (any grid) */
+    AF_PATH_SPLIT_BF16 = 3   /* the same direct DFT of Eq. 6 as a real-embedded GEMM on
+                                tcgen05 tensor cores, both operands split into BF16
+                                hi + lo (three products), FP32 accumulation; any grid,
+                                meant for narrow Doppler windows; pnorm must be 0 */
 };
 
 /* Number of doubles in a terms record (followed by M values of p_m). */
@@ -134,7 +138,8 @@ AF_API const char* af_last_error(const af_ctx* ctx);
 AF_API int32_t af_path_of(const af_ctx* ctx);
 
 /* Wait for the context's stream; returns AF_ERR_NONFINITE if any loss or
- * gradient since the last af_sync was NaN/Inf, AF_ERR_CUDA on a CUDA error. */
+ * gradient since the last af_sync was NaN/Inf, AF_ERR_TIMEOUT if a
+ * tensor-core pipeline wait gave up, AF_ERR_CUDA on a CUDA error. */
 AF_API af_status af_sync(af_ctx* ctx);
 
 /* Replace the quantization thresholds (host [K] floats, strictly increasing

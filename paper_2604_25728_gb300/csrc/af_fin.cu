@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
                 double* lg = a.log + ((size_t)o * a.evals_per_outer + a.eval_index) * 4;
                 lg[0] = s_terms[0]; lg[1] = s_terms[1]; lg[2] = s_terms[4]; lg[3] = s_terms[5];
             }
-            if (!isfinite(s_terms[0]) && a.err_flag) atomicExch(a.err_flag, 1);
+            if (!isfinite(s_terms[0]) && a.err_flag) atomicOr(a.err_flag, 1);
         }
     }
     __syncthreads();
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
             a.grad_u[e] = gu;
             bad |= !isfinite(gu);
         }
-        if (bad && a.err_flag) atomicExch(a.err_flag, 1);
+        if (bad && a.err_flag) atomicOr(a.err_flag, 1);
         return;
     }
 
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
                 for (int s = 0; s < S; ++s) tot += __ldcg(a.norm_part + (size_t)m * S + s);
                 s_scale = (tot > 0.0) ? (float)sqrt_d((double)N / tot) : 1.f;
                 a.row_ctr[m] = 0u;
-                if (!isfinite(s_scale) && a.err_flag) atomicExch(a.err_flag, 1);
+                if (!isfinite(s_scale) && a.err_flag) atomicOr(a.err_flag, 1);
             }
             __syncthreads();
             const float sc = s_scale;
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kFT) fin_kernel(const FinArgs a) {
         a.u[e] = uu;
         bad |= !isfinite(uu);
     }
-    if (bad && a.err_flag) atomicExch(a.err_flag, 1);
+    if (bad && a.err_flag) atomicOr(a.err_flag, 1);
 
     // waveform of the next evaluation (this element only; depends on u alone)
     if (a.next_wave != NEXT_NONE && in) {

@@ -1,0 +1,405 @@
+// af_gemm.cu -- forward pass on a narrow Doppler window as a tensor-core
+// contraction (sm_103a, tcgen05 + tensor memory).
+//
+// chi[(pair, d), j] = sum_n P[(pair, d), n] E[n, j]   (Eq. 6 restated per row)
+// with P = x_m(n) conj(h_l(n+k)) the lag products and E[n, j] = e^{j 2 pi nu_j n}.
+// Complex arithmetic is embedded in a real GEMM: the K index interleaves
+// (Re P(n), Im P(n)) and the output columns interleave (Re chi_j, Im chi_j),
+// so B[(n,0),(j,0)] = cos, B[(n,1),(j,0)] = -sin, B[(n,0),(j,1)] = sin,
+// B[(n,1),(j,1)] = cos of 2 pi nu_j n.
+//
+// Precision: both operands are split into BF16 pairs v = hi + lo and the
+// product is taken as Ah Bh + Ah Bl + Al Bh (the lo*lo term is below FP32
+// accumulation noise), accumulating in FP32 in tensor memory.
+//
+// One CTA owns 128 consecutive delays of one pair (the MMA M) and LB bins
+// (N = 2 LB columns).  Roles:
+//   warps 0-3  form the lag products of their row (thread = row = TMEM lane)
+//              for a chunk of 32 samples, split them and store them into a
+//              tensor-memory A stage (tcgen05.st); afterwards they read the
+//              accumulator back (tcgen05.ld) and run the sidelobe reduction.
+//   warp 4     allocates tensor memory; lane 0 issues the MMAs.
+//   warp 5     lane 0 streams the precomputed B images (hi | lo, already in
+//              the canonical no-swizzle K-major layout) with cp.async.bulk.
+// Stages are double-buffered with mbarriers; every wait is bounded and a
+// timeout sets bit 1 of the error flag and ends the kernel cleanly.
+#include <cuda_bf16.h>
+
+#include "af_common.cuh"
+#include "af_kernels.h"
+#include "af_tc.cuh"
+
+namespace af {
+
+constexpr int kGThreads = 192;
+constexpr int kStages = 2;
+constexpr int kTM = kGemmRows;             // 128 delays per tile
+constexpr int kSPC = kGemmSamples;         // 32 samples per chunk
+constexpr int kKC = 2 * kSPC;              // real K per chunk
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`.  Gives up when another role has
+// aborted (unless `drain`) or after kTimeoutNs, which aborts the CTA.
+__device__ __noinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, bool drain) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (!drain && *abort_flag) return false;
+        if (gtimer() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            if (err) atomicOr(err, 2);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x in the low half
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_lo_f(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi_f(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+          "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+          "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] * B[smem]: A from tensor memory (lane = row, K pairs per column).
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ bool gbetter(float a, long long ia, float b, long long ib) {
+    return a > b || (a == b && ia < ib);
+}
+
+__host__ __device__ constexpr int gemm_tmem_cols(int NC) {
+    return (NC + kStages * kKC <= 256) ? ((NC + kStages * kKC <= 128) ? 128 : 256) : 512;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kGThreads)
+fwd_gemm_kernel(const GemmArgs g) {
+    const FwdArgs<float2, float>& a = g.f;
+    constexpr int LB = NC / 2;
+    constexpr int STAGE_BYTES = NC * kKC * 2 * 2;    // hi | lo images
+    constexpr int TCOLS = gemm_tmem_cols(NC);
+    static_assert(NC % 32 == 0 && NC >= 32 && NC <= 256, "column tile");
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* bst = smem_raw;                                        // [kStages][STAGE_BYTES]
+    float2* xs = reinterpret_cast<float2*>(smem_raw + kStages * STAGE_BYTES);  // [kSPC * n_kc]
+    float2* hs = xs + kSPC * g.n_kc;                                      // [kSPC * n_kc + kTM]
+
+    __shared__ __align__(8) uint64_t bfull[kStages], afull[kStages], empty[kStages], accfull;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ float rk[4];
+    __shared__ long long ri[4];
+    __shared__ float2 rc[4];
+    __shared__ double red[2][4];
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int bx = blockIdx.x;
+    const int ct = bx % g.n_ct;
+    const int rest = bx / g.n_ct;
+    const int pair = rest / a.n_chunks;
+    const int tile = rest - pair * a.n_chunks;
+    const int m = pair / a.M, l = pair - m * a.M;
+    const int N = a.N, L = a.L, D = a.D;
+    const int d0 = tile * kTM;
+    const int k_first = a.k_lo + d0;
+    const int k_last = a.k_lo + min(D, d0 + kTM) - 1;
+    const int n_begin = max(0, -k_last), n_end = min(N, N - k_first);
+    const int c0 = n_begin / kSPC;
+    const int nch = (n_end + kSPC - 1) / kSPC - c0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&bfull[s], 1);
+            tc::mbar_init(&afull[s], kTM);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(&accfull, 1);
+        s_abort = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == 4) {
+        __syncwarp();
+        tc::tmem_alloc(&s_tmem, TCOLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = s_tmem;
+    volatile int* abort_flag = &s_abort;
+
+    const unsigned char* img = reinterpret_cast<const unsigned char*>(g.bimg) +
+                               ((size_t)ct * g.n_kc + c0) * (size_t)STAGE_BYTES;
+
+    if (warp == 5) {
+        // ---------------------------------------------------- B loader --
+        int issued = 0;
+        if (lane == 0) {
+            // the tables are constant: the first stages load before the
+            // previous kernel in the stream has finished
+            const int pro = min(kStages, nch);
+            for (int i = 0; i < pro; ++i) {
+                tc::mbar_arrive_expect_tx(&bfull[i], STAGE_BYTES);
+                tc::bulk_g2s(bst + i * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[i]);
+            }
+            issued = pro;
+        }
+        pdl_wait();
+        pdl_trigger();
+        if (lane == 0) {
+            for (int i = kStages; i < nch; ++i) {
+                const int s = i % kStages;
+                if (!gwait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, g.err, false)) break;
+                tc::mbar_arrive_expect_tx(&bfull[s], STAGE_BYTES);
+                tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
+                issued = i + 1;
+            }
+            // every copy this CTA issued has landed before it exits
+            for (int i = max(0, issued - kStages); i < issued; ++i)
+                gwait(&bfull[i % kStages], (i / kStages) & 1, abort_flag, g.err, true);
+        }
+    } else if (warp == 4) {
+        // ------------------------------------------------- MMA issuer --
+        pdl_wait();
+        pdl_trigger();
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16(kTM, NC);
+            const uint32_t bsm = tc::smem_u32(bst);
+            for (int i = 0; i < nch; ++i) {
+                const int s = i % kStages;
+                const uint32_t ph = (i / kStages) & 1;
+                if (!gwait(&bfull[s], ph, abort_flag, g.err, false)) break;
+                if (!gwait(&afull[s], ph, abort_flag, g.err, false)) break;
+                tc::fence_after_sync();
+                const uint32_t a_hi = tbase + NC + s * kKC;
+                const uint32_t a_lo = a_hi + kSPC;
+                const uint32_t b_hi = bsm + s * STAGE_BYTES;
+                const uint32_t b_lo = b_hi + NC * kKC * 2;
+#pragma unroll
+                for (int q = 0; q < kKC / 16; ++q) {
+                    const uint64_t dh = tc::smem_desc(b_hi + q * 256, 128, (kKC / 8) * 128);
+                    const uint64_t dl = tc::smem_desc(b_lo + q * 256, 128, (kKC / 8) * 128);
+                    mma_ts(tbase, a_hi + 8 * q, dh, idesc, (i > 0 || q > 0) ? 1u : 0u);
+                    mma_ts(tbase, a_hi + 8 * q, dl, idesc, 1u);
+                    mma_ts(tbase, a_lo + 8 * q, dh, idesc, 1u);
+                }
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(&accfull);
+            gwait(&accfull, 0, abort_flag, g.err, true);
+        }
+    } else {
+        // ------------------------------------ producers and epilogue --
+        pdl_wait();
+        pdl_trigger();
+        if (a.ctr_inc != nullptr && bx == 0 && tid == 0) a.ctr_inc[0] += 1;
+        const float2* xm = a.x + (size_t)m * N;
+        const float2* hl = a.h + (size_t)l * N;
+        const int nx = kSPC * nch, nh = kSPC * nch + kTM;
+        for (int i = tid; i < nh; i += kTM) {
+            const int p = kSPC * c0 + k_first + i;
+            hs[i] = (p >= 0 && p < N) ? hl[p] : make_float2(0.f, 0.f);
+            if (i < nx) {
+                const int n = kSPC * c0 + i;
+                xs[i] = (n < N) ? xm[n] : make_float2(0.f, 0.f);
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kTM) : "memory");
+
+        const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+        bool ok = true;
+        for (int i = 0; i < nch; ++i) {
+            const int s = i % kStages;
+            if (i >= kStages) {
+                // the warp agrees before its aligned tensor-memory stores
+                const bool w = gwait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, g.err, false);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                tc::fence_after_sync();
+            }
+            uint32_t hi[kSPC], lo[kSPC];
+            const float2* xc = xs + i * kSPC;
+            const float2* hc = hs + i * kSPC + tid;
+#pragma unroll
+            for (int t = 0; t < kSPC; ++t) {
+                const float2 xv = xc[t], hv = hc[t];
+                const float re = fmaf(xv.x, hv.x, xv.y * hv.y);
+                const float im = fmaf(xv.y, hv.x, -(xv.x * hv.y));
+                const uint32_t ph = pack_bf16(re, im);
+                hi[t] = ph;
+                lo[t] = pack_bf16(re - bf16_lo_f(ph), im - bf16_hi_f(ph));
+            }
+            const uint32_t acol = trow + NC + s * kKC;
+            tmem_st32(acol, hi);
+            tmem_st32(acol + kSPC, lo);
+            tmem_st_wait();
+            tc::fence_before_sync();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&afull[s])) : "memory");
+        }
+
+        // ---- epilogue: accumulator -> sidelobe reduction (Eqs. 7-9) ----
+        float best = -1.f;
+        long long best_idx = 0x7fffffffffffffffLL;
+        float2 best_c = make_float2(0.f, 0.f);
+        const bool acc_ready = ok && gwait(&accfull, 0, abort_flag, g.err, false);
+        if (__all_sync(0xffffffffu, acc_ready)) {
+            tc::fence_after_sync();
+            const int d = d0 + tid;
+            const int k = a.k_lo + d;
+            const bool row_ok = d < D && !(m == l && k == 0);
+            const bool dump = a.mode == FWD_DUMP;
+#pragma unroll 1
+            for (int cc = 0; cc < NC / 32; ++cc) {
+                float v[32];
+                tc::tmem_ld32(trow + cc * 32, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    const int jj = ct * LB + cc * 16 + b;
+                    const float re = v[2 * b], im = v[2 * b + 1];
+                    if (dump) {
+                        if (d < D && jj < L) a.chi_out[((size_t)pair * D + d) * L + jj] = make_float2(re, im);
+                        continue;
+                    }
+                    if (!row_ok || jj >= L) continue;
+                    float key = re * re + im * im;
+                    if (a.weight_mode != WM_UNIFORM) {
+                        const float w = __ldg(a.wmap + (size_t)d * L + jj);
+                        key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : -1.f;
+                    }
+                    const long long cell = ((long long)pair * D + d) * L + jj;
+                    if (gbetter(key, cell, best, best_idx)) { best = key; best_idx = cell; best_c = make_float2(re, im); }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        if (a.mode != FWD_DUMP) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
+                const float ocx = __shfl_xor_sync(0xffffffffu, best_c.x, o);
+                const float ocy = __shfl_xor_sync(0xffffffffu, best_c.y, o);
+                if (gbetter(ob, oi, best, best_idx)) { best = ob; best_idx = oi; best_c = make_float2(ocx, ocy); }
+            }
+            if (lane == 0) { rk[warp] = best; ri[warp] = best_idx; rc[warp] = best_c; }
+            asm volatile("bar.sync 1, %0;" ::"n"(kTM) : "memory");
+            if (tid == 0) {
+                float b = rk[0];
+                long long bi = ri[0];
+                float2 bc = rc[0];
+                for (int w = 1; w < 4; ++w)
+                    if (gbetter(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; bc = rc[w]; }
+                a.pkey[bx] = b;
+                a.pidx[bx] = (b >= 0.f) ? bi : -1;
+                if (a.pchi) a.pchi[bx] = bc;
+                if (a.pvmax) { a.pvmax[bx] = 0.f; a.psum[bx] = 0.f; }
+            }
+        }
+        // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) in FP64 (SNRL, Eq. 38)
+        if (a.cdiag != nullptr && m == l && tile == 0 && ct == 0) {
+            double sr = 0.0, si = 0.0;
+            for (int n = tid; n < N; n += kTM) {
+                const float2 xv = xm[n], hv = hl[n];
+                const double xr = xv.x, xi = xv.y, hr = hv.x, hi_ = hv.y;
+                sr += xr * hr + xi * hi_;
+                si += xi * hr - xr * hi_;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
+            asm volatile("bar.sync 1, %0;" ::"n"(kTM) : "memory");
+            if (tid == 0)
+                a.cdiag[m] = make_double2(red[0][0] + red[0][1] + red[0][2] + red[0][3],
+                                          red[1][0] + red[1][1] + red[1][2] + red[1][3]);
+        }
+    }
+
+    __syncthreads();
+    if (warp == 4) {
+        __syncwarp();
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, TCOLS);
+    }
+}
+
+int gemm_bins_per_tile(int L) {
+    int lb = 16;
+    while (lb < L && lb < 128) lb <<= 1;
+    return lb;
+}
+
+// Dynamic shared memory of a CTA.  It is padded so that the CTAs that fit on
+// an SM never ask for more tensor memory than the SM's 512 columns (at most
+// two CTAs of 256 columns, one of 512), so no allocation has to wait.
+int gemm_smem_bytes(int L, int N) {
+    const int NC = 2 * gemm_bins_per_tile(L);
+    const int n_kc = (N + kSPC - 1) / kSPC;
+    const int need = kStages * NC * kKC * 4 + (int)sizeof(float2) * (2 * kSPC * n_kc + kTM);
+    const int floor_bytes = (gemm_tmem_cols(NC) == 512) ? 116 * 1024 : 77 * 1024;
+    return need > floor_bytes ? need : floor_bytes;
+}
+
+template <int NC>
+static cudaError_t launch_nc(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
+    auto kern = fwd_gemm_kernel<NC>;
+    cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
+    if (e != cudaSuccess || prepare_only) return e;
+    const int grid = g.f.M * g.f.M * g.f.n_chunks * g.n_ct;
+    return launch_ex(kern, dim3(grid), dim3(kGThreads), smem, s, g.f.pdl != 0, g);
+}
+
+static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only) {
+    const int smem = gemm_smem_bytes(g.f.L, g.f.N);
+    switch (2 * gemm_bins_per_tile(g.f.L)) {
+        case 32: return launch_nc<32>(g, smem, s, prepare_only);
+        case 64: return launch_nc<64>(g, smem, s, prepare_only);
+        case 128: return launch_nc<128>(g, smem, s, prepare_only);
+        case 256: return launch_nc<256>(g, smem, s, prepare_only);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t gemm_prepare(int L, int N) {
+    GemmArgs g{};
+    g.f.L = L;
+    g.f.N = N;
+    return dispatch(g, nullptr, true);
+}
+
+cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s) {
+    if (g.f.n_chunks * kTM < g.f.D || g.n_kc * kSPC < g.f.N) return cudaErrorInvalidValue;
+    return dispatch(g, s, false);
+}
+
+}  // namespace af

@@ -25,6 +25,60 @@ inline void phasor(double t, double* re, double* im) {
     *im = sin(kTwoPi * f);
 }
 
+// BF16 round-to-nearest-even of a finite float, and back.
+inline uint16_t bf16_rne(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+inline float bf16_float(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// Images of the real-embedded DFT matrix for the tensor-core path, one per
+// (column tile, chunk of 32 samples), each [hi | lo] of 2 LB rows x 64 K in
+// the canonical K-major no-swizzle layout: 8x8 BF16 core matrices, 128 B
+// apart along K, 8 core matrices (1 KB) apart between row groups.  Row
+// 2j + u is output bin j (u = 0 real, 1 imaginary part), K index 2s + t is
+// sample s of the chunk (t = 0 real, 1 imaginary part of the lag product):
+//   (t,u) = (0,0): cos, (1,0): -sin, (0,1): sin, (1,1): cos  of 2 pi nu_j n.
+// Each value v (built in FP64) is stored as hi = bf16(v), lo = bf16(v - hi).
+void gemm_build_image(const std::vector<double>& nu, int N, std::vector<uint16_t>& img) {
+    const int L = (int)nu.size();
+    const int LB = af::gemm_bins_per_tile(L), NC = 2 * LB, SPC = af::kGemmSamples, KC = 2 * SPC;
+    const int n_ct = (L + LB - 1) / LB, n_kc = (N + SPC - 1) / SPC;
+    const size_t part = (size_t)NC * KC;
+    img.assign((size_t)n_ct * n_kc * 2 * part, 0);
+    for (int ct = 0; ct < n_ct; ++ct)
+        for (int c = 0; c < n_kc; ++c) {
+            uint16_t* hi = img.data() + ((size_t)ct * n_kc + c) * 2 * part;
+            uint16_t* lo = hi + part;
+            for (int sm = 0; sm < SPC; ++sm) {
+                const int n = c * SPC + sm;
+                if (n >= N) break;
+                for (int j = 0; j < LB; ++j) {
+                    const int jj = ct * LB + j;
+                    if (jj >= L) break;
+                    double cs, sn;
+                    phasor(nu[jj] * n, &cs, &sn);
+                    const double val[2][2] = {{cs, sn}, {-sn, cs}};   // [t][u]
+                    for (int t = 0; t < 2; ++t)
+                        for (int u = 0; u < 2; ++u) {
+                            const int ci = 2 * j + u, kk = 2 * sm + t;
+                            const size_t off = (size_t)(ci / 8) * (KC / 8) * 64 + (kk / 8) * 64 + (ci % 8) * 8 + kk % 8;
+                            const uint16_t h16 = bf16_rne((float)val[t][u]);
+                            hi[off] = h16;
+                            lo[off] = bf16_rne((float)(val[t][u] - (double)bf16_float(h16)));
+                        }
+                }
+            }
+        }
+}
+
 struct FftPassInfo { int R, NS; };
 
 // Host mirror of the device FFT plan (radix-E passes, then the remainder).
@@ -62,6 +116,8 @@ struct af_ctx {
     float2* tw = nullptr;      // FFT twiddles
     float2* wL = nullptr;      // [L] e^{j 2 pi i / L}
     float2* E = nullptr;       // [N][L] e^{j 2 pi nu_j n} (DFT path)
+    uint16_t* bimg = nullptr;  // BF16 hi/lo images of E (tensor-core path)
+    int gemm_n_ct = 0, gemm_n_kc = 0;
     double2* pre64 = nullptr;
     double2* tw64 = nullptr;
     double2* E64 = nullptr;
@@ -162,7 +218,8 @@ static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
                     c->xs, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
-                    c->ctr, c->best2, c->log, c->pchi, c->norm_part, c->row_ctr, c->adj_part, c->dense};
+                    c->ctr, c->best2, c->log, c->pchi, c->norm_part, c->row_ctr, c->adj_part, c->dense,
+                    c->bimg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -228,10 +285,6 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     *out = nullptr;
     std::string why;
     if (validate(cfg, &why) != AF_OK) { g_init_error = why; return AF_ERR_INVALID_ARG; }
-    if (cfg->path == AF_PATH_SPLIT_BF16) {
-        g_init_error = "AF_PATH_SPLIT_BF16 is not available in this build";
-        return AF_ERR_UNIMPLEMENTED;
-    }
 
     af_ctx* c = new af_ctx();
     c->cfg = *cfg;
@@ -269,6 +322,10 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         return fail(AF_ERR_UNIMPLEMENTED);
     }
     c->path = (cfg->path == AF_PATH_AUTO) ? (uniform ? AF_PATH_FFT : AF_PATH_DFT) : cfg->path;
+    if (c->path == AF_PATH_SPLIT_BF16 && gemm_smem_bytes(L, N) > 227 * 1024) {
+        c->err = "AF_PATH_SPLIT_BF16: N too large for the shared-memory staging";
+        return fail(AF_ERR_UNIMPLEMENTED);
+    }
     c->grid_fft = uniform;
     if (cfg->pnorm > 0.0) {
         // the dense adjoint of the p-norm loss runs on the FFT grid
@@ -345,6 +402,14 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
             }
         if ((s = upload(c, &c->E, E)) || (s = upload(c, &c->E64, E64))) return fail(s);
     }
+    if (c->path == AF_PATH_SPLIT_BF16) {
+        std::vector<uint16_t> img;
+        gemm_build_image(c->nu, N, img);
+        if ((s = upload(c, &c->bimg, img))) return fail(s);
+        const int LB = gemm_bins_per_tile(L);
+        c->gemm_n_ct = (L + LB - 1) / LB;
+        c->gemm_n_kc = (N + kGemmSamples - 1) / kGemmSamples;
+    }
     if (cfg->weights) {
         c->wmap_host.assign(cfg->weights, cfg->weights + (size_t)c->D * L);
         if ((s = upload(c, &c->wmap, c->wmap_host))) return fail(s);
@@ -357,7 +422,8 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
 
     // kernels' shared-memory limits are raised here, outside any graph capture
     {
-        cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e) : dft_prepare_f32(N);
+        cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e)
+                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N) : dft_prepare_f32(N);
         if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
         if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
         if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
@@ -373,6 +439,10 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         c->rows_per_chunk = RS * it;
         c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
         c->ctas_per_pair = c->n_chunks;
+    } else if (c->path == AF_PATH_SPLIT_BF16) {
+        c->rows_per_chunk = kGemmRows;
+        c->n_chunks = (c->D + kGemmRows - 1) / kGemmRows;
+        c->ctas_per_pair = c->n_chunks * c->gemm_n_ct;
     } else {
         c->rows_per_chunk = dft_rows_per_cta();
         c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
@@ -440,6 +510,7 @@ extern "C" af_status af_sync(af_ctx* c) {
     CK(c, cudaMemcpy(&flag, c->errflag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         CK(c, cudaMemset(c->errflag, 0, sizeof(int)));
+        if (flag & 2) FAIL(c, AF_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
         FAIL(c, AF_ERR_NONFINITE, "a loss or gradient was NaN or Inf");
     }
     return AF_OK;
@@ -477,6 +548,15 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
 }
 
 static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaStream_t s) {
+    if (c->path == AF_PATH_SPLIT_BF16) {
+        GemmArgs g{};
+        g.f = a;
+        g.bimg = c->bimg;
+        g.err = c->errflag;
+        g.n_ct = c->gemm_n_ct;
+        g.n_kc = c->gemm_n_kc;
+        return launch_fwd_gemm(g, s);
+    }
     return (c->path == AF_PATH_FFT) ? launch_fwd_fft_f32(a, s) : launch_fwd_dft_f32(a, s);
 }
 
