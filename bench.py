@@ -32,6 +32,8 @@ UNIT = "evals/s"
 PROFILES = os.path.join(ROOT, "profiles")
 FWD_SOURCES = ["paper_2604_25728_gb300/csrc/af_fft.cu", "paper_2604_25728_gb300/csrc/af_common.cuh",
                "paper_2604_25728_gb300/csrc/af_kernels.h"]
+GEMM_SOURCES = ["paper_2604_25728_gb300/csrc/af_gemm.cu", "paper_2604_25728_gb300/csrc/af_tc.cuh",
+                "paper_2604_25728_gb300/csrc/af_common.cuh", "paper_2604_25728_gb300/csrc/af_kernels.h"]
 
 
 def _args():
@@ -156,6 +158,24 @@ def _fwd_flops(w) -> float:
 def _fp32_peak_tflops() -> tuple[float, str]:
     # 152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2.070 GHz maximum SM clock
     return 152 * 128 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+
+
+def _split_flops(w) -> float:
+    """Algorithmic tensor FLOPs of one forward launch on the split-BF16 path:
+    8 real FLOPs per complex multiply-add of a valid lag product with each of
+    the L phasors, times the three BF16 products (hi.hi, hi.lo, lo.hi)."""
+    P = w.M * w.M
+    n = np.arange(w.k_lo, w.k_hi + 1)
+    valid = np.clip(w.N - np.abs(n), 0, None).sum()
+    return 3 * 8.0 * P * valid * w.L
+
+
+def _measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def _source_hash(paths) -> str:
@@ -366,6 +386,7 @@ def run_ours(args):
 
     best = st.best.cpu().numpy()
     acc = ctx.af_eval_hard(st.u, st.h)
+    tensor = _tensor_path(api, wl, dev, stream) if rank == 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -385,6 +406,7 @@ def run_ours(args):
                          "algorithmic_flops_per_launch": flops, "launch_us": fwd_s * 1e6,
                          "traffic": traffic, "kernel_source_hash": khash},
             "cpu_baseline": cpu,
+            "tensor_path": tensor,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per sqngd_step call: counters, best-record copy in, hard waveform,
             # the graph (forward + finish per evaluation), best-record copy out
@@ -399,6 +421,55 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _tensor_path(api, wl, dev, stream):
+    """The narrow-window workload (M=8, N=1024, |k| <= 255, 64 bins on
+    |nu| <= 0.05) on the tcgen05 split-BF16 path, beside the FP32 SIMT DFT
+    path: forward launch time, tensor roofline, loss+grad evaluations/s."""
+    import torch
+
+    w = wl.precision()
+    x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
+    h = x.clone()
+    gx = torch.empty_like(x)
+    gh = torch.empty_like(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms)) / 1e3
+
+    out = {"workload": w.name}
+    for name, path, reps in (("split_bf16", api.AF_PATH_SPLIT_BF16, 200), ("fp32_dft", api.AF_PATH_DFT, 40)):
+        c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, path=path)
+        fwd = timed(lambda: c.af_forward(x, h), reps)
+        ev = timed(lambda: c.af_loss_grad_xh(x, h, grad_x=gx, grad_h=gh), reps)
+        c.af_sync()
+        c.close()
+        out[name] = {"fwd_launch_us": fwd * 1e6, "loss_grad_evals_per_s": 1.0 / ev}
+    peaks = _measured_peaks()
+    peak = peaks.get("bf16_tflops")
+    flops = _split_flops(w)
+    achieved = flops / (out["split_bf16"]["fwd_launch_us"] * 1e-6) / 1e12
+    khash = _source_hash(GEMM_SOURCES)
+    out["roofline"] = {"bound": "tensor", "kernel": "fwd_gemm_kernel (af_forward, AF_PATH_SPLIT_BF16)",
+                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": (achieved / peak) if peak else None,
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS), of measured",
+                       "algorithmic_flops_per_launch": flops, "kernel_source_hash": khash}
+    out["speedup_fwd_vs_fp32_dft"] = out["fp32_dft"]["fwd_launch_us"] / out["split_bf16"]["fwd_launch_us"]
+    return out
 
 
 def main():

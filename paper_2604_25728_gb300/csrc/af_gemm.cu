@@ -31,11 +31,7 @@
 
 namespace af {
 
-constexpr int kGThreads = 192;
-constexpr int kStages = 2;
 constexpr int kTM = kGemmRows;             // 128 delays per tile
-constexpr int kSPC = kGemmSamples;         // 32 samples per chunk
-constexpr int kKC = 2 * kSPC;              // real K per chunk
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -67,7 +63,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
 __device__ __forceinline__ float bf16_lo_f(uint32_t v) { return __uint_as_float(v << 16); }
 __device__ __forceinline__ float bf16_hi_f(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+template <int NR> __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[NR]);
+template <> __device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+template <> __device__ __forceinline__ void tmem_st<32>(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
         "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
@@ -95,40 +100,52 @@ __device__ __forceinline__ bool gbetter(float a, long long ia, float b, long lon
     return a > b || (a == b && ia < ib);
 }
 
-__host__ __device__ constexpr int gemm_tmem_cols(int NC) {
-    return (NC + kStages * kKC <= 256) ? ((NC + kStages * kKC <= 128) ? 128 : 256) : 512;
+// Tensor-memory columns of a CTA: T accumulators of NC columns plus ST A
+// stages of T tiles x (SPC hi + SPC lo) columns, rounded up to a power of
+// two (0 if more than 512).
+__host__ __device__ constexpr int gemm_tmem_cols(int NC, int SPC, int ST, int T) {
+    return (T * NC + 2 * SPC * ST * T <= 128) ? 128 : (T * NC + 2 * SPC * ST * T <= 256) ? 256
+         : (T * NC + 2 * SPC * ST * T <= 512) ? 512 : 0;
 }
 
-template <int NC>
-__global__ void __launch_bounds__(kGThreads)
+template <int NC, int kSPC, int kStages, int T>
+__global__ void __launch_bounds__(32 * (4 * T + 2), 1)
 fwd_gemm_kernel(const GemmArgs g) {
     const FwdArgs<float2, float>& a = g.f;
+    constexpr int kKC = 2 * kSPC;                    // real K per chunk
     constexpr int LB = NC / 2;
+    constexpr int NPROD = kTM * T;                   // producer / epilogue threads
+    constexpr int WMMA = 4 * T, WLOAD = 4 * T + 1;   // MMA and loader warps
     constexpr int STAGE_BYTES = NC * kKC * 2 * 2;    // hi | lo images
-    constexpr int TCOLS = gemm_tmem_cols(NC);
+    constexpr int TCOLS = gemm_tmem_cols(NC, kSPC, kStages, T);
     static_assert(NC % 32 == 0 && NC >= 32 && NC <= 256, "column tile");
+    static_assert(TCOLS > 0 && kSPC % 8 == 0, "stage shape");
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* bst = smem_raw;                                        // [kStages][STAGE_BYTES]
-    float2* xs = reinterpret_cast<float2*>(smem_raw + kStages * STAGE_BYTES);  // [kSPC * n_kc]
-    float2* hs = xs + kSPC * g.n_kc;                                      // [kSPC * n_kc + kTM]
+    const int XH = 2 * kSPC * g.n_kc + kTM;                               // per tile: xs, then hs
+    float2* xh_base = reinterpret_cast<float2*>(smem_raw + kStages * STAGE_BYTES);
 
     __shared__ __align__(8) uint64_t bfull[kStages], afull[kStages], empty[kStages], accfull;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    __shared__ float rk[4];
-    __shared__ long long ri[4];
-    __shared__ float2 rc[4];
-    __shared__ double red[2][4];
+    __shared__ float rk[T][4];
+    __shared__ long long ri[T][4];
+    __shared__ float2 rc[T][4];
+    __shared__ double red[T][2][4];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    // CTAs are ordered pair-group-fastest, so the CTAs of a cluster share the
+    // delay block and column tile -- hence every B image -- and differ in pairs.
+    // A CTA owns the T consecutive pairs pg*T .. pg*T + T-1 of one delay block.
     const int bx = blockIdx.x;
-    const int ct = bx % g.n_ct;
-    const int rest = bx / g.n_ct;
-    const int pair = rest / a.n_chunks;
-    const int tile = rest - pair * a.n_chunks;
-    const int m = pair / a.M, l = pair - m * a.M;
+    const int P = a.M * a.M;
+    const int PG = P / T;
+    const int pg = bx % PG;
+    const int rest = bx / PG;
+    const int ct = rest % g.n_ct;
+    const int tile = rest / g.n_ct;
     const int N = a.N, L = a.L, D = a.D;
     const int d0 = tile * kTM;
     const int k_first = a.k_lo + d0;
@@ -136,24 +153,29 @@ fwd_gemm_kernel(const GemmArgs g) {
     const int n_begin = max(0, -k_last), n_end = min(N, N - k_first);
     const int c0 = n_begin / kSPC;
     const int nch = (n_end + kSPC - 1) / kSPC - c0;
+    const int C = g.csize;
+    const uint32_t crank = (C > 1) ? tc::cluster_ctarank() : 0u;
+    const uint16_t cmask = (uint16_t)((1u << C) - 1u);
+    const int SLB = STAGE_BYTES / C;                           // this CTA's slice of every stage
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(&bfull[s], 1);
-            tc::mbar_init(&afull[s], kTM);
-            tc::mbar_init(&empty[s], 1);
+            tc::mbar_init(&afull[s], NPROD);
+            tc::mbar_init(&empty[s], C);   // one MMA commit from every CTA of the cluster
         }
         tc::mbar_init(&accfull, 1);
         s_abort = 0;
         tc::mbar_fence_init();
     }
-    if (warp == 4) {
+    if (warp == WMMA) {
         __syncwarp();
         tc::tmem_alloc(&s_tmem, TCOLS);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
-    __syncthreads();
+    if (C > 1) tc::cluster_sync();   // barriers initialised cluster-wide before any multicast
+    else __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = s_tmem;
     volatile int* abort_flag = &s_abort;
@@ -161,17 +183,24 @@ fwd_gemm_kernel(const GemmArgs g) {
     const unsigned char* img = reinterpret_cast<const unsigned char*>(g.bimg) +
                                ((size_t)ct * g.n_kc + c0) * (size_t)STAGE_BYTES;
 
-    if (warp == 5) {
+    if (warp == WLOAD) {
         // ---------------------------------------------------- B loader --
+        // Stage s of chunk i: this CTA expects the whole stage on its own
+        // barrier and copies its slice into every CTA of the cluster.
+        auto issue = [&](int i, int s) {
+            tc::mbar_arrive_expect_tx(&bfull[s], STAGE_BYTES);
+            if (C > 1)
+                tc::bulk_g2s_mc(bst + s * STAGE_BYTES + crank * SLB, img + (size_t)i * STAGE_BYTES + crank * SLB,
+                                SLB, &bfull[s], cmask);
+            else
+                tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
+        };
         int issued = 0;
         if (lane == 0) {
             // the tables are constant: the first stages load before the
             // previous kernel in the stream has finished
             const int pro = min(kStages, nch);
-            for (int i = 0; i < pro; ++i) {
-                tc::mbar_arrive_expect_tx(&bfull[i], STAGE_BYTES);
-                tc::bulk_g2s(bst + i * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[i]);
-            }
+            for (int i = 0; i < pro; ++i) issue(i, i);
             issued = pro;
         }
         pdl_wait();
@@ -179,16 +208,19 @@ fwd_gemm_kernel(const GemmArgs g) {
         if (lane == 0) {
             for (int i = kStages; i < nch; ++i) {
                 const int s = i % kStages;
+                // every CTA of the cluster has finished with stage s
                 if (!gwait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, g.err, false)) break;
-                tc::mbar_arrive_expect_tx(&bfull[s], STAGE_BYTES);
-                tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
+                issue(i, s);
                 issued = i + 1;
             }
-            // every copy this CTA issued has landed before it exits
+            // every stage this CTA expects has landed, and every MMA commit
+            // the cluster sends to this CTA has arrived, before it exits
             for (int i = max(0, issued - kStages); i < issued; ++i)
                 gwait(&bfull[i % kStages], (i / kStages) & 1, abort_flag, g.err, true);
+            for (int i = max(0, nch - kStages); i < nch; ++i)
+                gwait(&empty[i % kStages], (i / kStages) & 1, abort_flag, g.err, true);
         }
-    } else if (warp == 4) {
+    } else if (warp == WMMA) {
         // ------------------------------------------------- MMA issuer --
         pdl_wait();
         pdl_trigger();
@@ -201,19 +233,24 @@ fwd_gemm_kernel(const GemmArgs g) {
                 if (!gwait(&bfull[s], ph, abort_flag, g.err, false)) break;
                 if (!gwait(&afull[s], ph, abort_flag, g.err, false)) break;
                 tc::fence_after_sync();
-                const uint32_t a_hi = tbase + NC + s * kKC;
-                const uint32_t a_lo = a_hi + kSPC;
                 const uint32_t b_hi = bsm + s * STAGE_BYTES;
                 const uint32_t b_lo = b_hi + NC * kKC * 2;
 #pragma unroll
-                for (int q = 0; q < kKC / 16; ++q) {
-                    const uint64_t dh = tc::smem_desc(b_hi + q * 256, 128, (kKC / 8) * 128);
-                    const uint64_t dl = tc::smem_desc(b_lo + q * 256, 128, (kKC / 8) * 128);
-                    mma_ts(tbase, a_hi + 8 * q, dh, idesc, (i > 0 || q > 0) ? 1u : 0u);
-                    mma_ts(tbase, a_hi + 8 * q, dl, idesc, 1u);
-                    mma_ts(tbase, a_lo + 8 * q, dh, idesc, 1u);
+                for (int t = 0; t < T; ++t) {
+                    const uint32_t d_t = tbase + t * NC;
+                    const uint32_t a_hi = tbase + T * NC + (s * T + t) * kKC;
+                    const uint32_t a_lo = a_hi + kSPC;
+#pragma unroll
+                    for (int q = 0; q < kKC / 16; ++q) {
+                        const uint64_t dh = tc::smem_desc(b_hi + q * 256, 128, (kKC / 8) * 128);
+                        const uint64_t dl = tc::smem_desc(b_lo + q * 256, 128, (kKC / 8) * 128);
+                        mma_ts(d_t, a_hi + 8 * q, dh, idesc, (i > 0 || q > 0) ? 1u : 0u);
+                        mma_ts(d_t, a_hi + 8 * q, dl, idesc, 1u);
+                        mma_ts(d_t, a_lo + 8 * q, dh, idesc, 1u);
+                    }
                 }
-                tc::mma_commit(&empty[s]);
+                if (C > 1) tc::mma_commit_mc(&empty[s], cmask);
+                else tc::mma_commit(&empty[s]);
             }
             tc::mma_commit(&accfull);
             gwait(&accfull, 0, abort_flag, g.err, true);
@@ -223,10 +260,16 @@ fwd_gemm_kernel(const GemmArgs g) {
         pdl_wait();
         pdl_trigger();
         if (a.ctr_inc != nullptr && bx == 0 && tid == 0) a.ctr_inc[0] += 1;
+        const int t = tid / kTM, r = tid % kTM;          // this thread's tile and row
+        const int pair = pg * T + t;
+        const int m = pair / a.M, l = pair - m * a.M;
+        const int ob = (pair * a.n_chunks + tile) * g.n_ct + ct;   // partial record (pair-major)
+        float2* xs = xh_base + t * XH;                   // [kSPC * n_kc]
+        float2* hs = xs + kSPC * g.n_kc;                 // [kSPC * n_kc + kTM]
         const float2* xm = a.x + (size_t)m * N;
         const float2* hl = a.h + (size_t)l * N;
         const int nx = kSPC * nch, nh = kSPC * nch + kTM;
-        for (int i = tid; i < nh; i += kTM) {
+        for (int i = r; i < nh; i += kTM) {
             const int p = kSPC * c0 + k_first + i;
             hs[i] = (p >= 0 && p < N) ? hl[p] : make_float2(0.f, 0.f);
             if (i < nx) {
@@ -234,9 +277,10 @@ fwd_gemm_kernel(const GemmArgs g) {
                 xs[i] = (n < N) ? xm[n] : make_float2(0.f, 0.f);
             }
         }
-        asm volatile("bar.sync 1, %0;" ::"n"(kTM) : "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
 
-        const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+        const int wq = warp & 3;                          // lane quarter of tensor memory
+        const uint32_t trow = tbase + ((uint32_t)(wq * 32) << 16);
         bool ok = true;
         for (int i = 0; i < nch; ++i) {
             const int s = i % kStages;
@@ -248,19 +292,19 @@ fwd_gemm_kernel(const GemmArgs g) {
             }
             uint32_t hi[kSPC], lo[kSPC];
             const float2* xc = xs + i * kSPC;
-            const float2* hc = hs + i * kSPC + tid;
+            const float2* hc = hs + i * kSPC + r;
 #pragma unroll
-            for (int t = 0; t < kSPC; ++t) {
-                const float2 xv = xc[t], hv = hc[t];
+            for (int u = 0; u < kSPC; ++u) {
+                const float2 xv = xc[u], hv = hc[u];
                 const float re = fmaf(xv.x, hv.x, xv.y * hv.y);
                 const float im = fmaf(xv.y, hv.x, -(xv.x * hv.y));
                 const uint32_t ph = pack_bf16(re, im);
-                hi[t] = ph;
-                lo[t] = pack_bf16(re - bf16_lo_f(ph), im - bf16_hi_f(ph));
+                hi[u] = ph;
+                lo[u] = pack_bf16(re - bf16_lo_f(ph), im - bf16_hi_f(ph));
             }
-            const uint32_t acol = trow + NC + s * kKC;
-            tmem_st32(acol, hi);
-            tmem_st32(acol + kSPC, lo);
+            const uint32_t acol = trow + T * NC + (s * T + t) * kKC;
+            tmem_st<kSPC>(acol, hi);
+            tmem_st<kSPC>(acol + kSPC, lo);
             tmem_st_wait();
             tc::fence_before_sync();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&afull[s])) : "memory");
@@ -273,14 +317,14 @@ fwd_gemm_kernel(const GemmArgs g) {
         const bool acc_ready = ok && gwait(&accfull, 0, abort_flag, g.err, false);
         if (__all_sync(0xffffffffu, acc_ready)) {
             tc::fence_after_sync();
-            const int d = d0 + tid;
+            const int d = d0 + r;
             const int k = a.k_lo + d;
             const bool row_ok = d < D && !(m == l && k == 0);
             const bool dump = a.mode == FWD_DUMP;
 #pragma unroll 1
             for (int cc = 0; cc < NC / 32; ++cc) {
                 float v[32];
-                tc::tmem_ld32(trow + cc * 32, v);
+                tc::tmem_ld32(trow + t * NC + cc * 32, v);
                 tc::tmem_ld_wait();
 #pragma unroll
                 for (int b = 0; b < 16; ++b) {
@@ -304,49 +348,54 @@ fwd_gemm_kernel(const GemmArgs g) {
         tc::fence_before_sync();
         if (a.mode != FWD_DUMP) {
             for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const float obk = __shfl_xor_sync(0xffffffffu, best, o);
                 const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
                 const float ocx = __shfl_xor_sync(0xffffffffu, best_c.x, o);
                 const float ocy = __shfl_xor_sync(0xffffffffu, best_c.y, o);
-                if (gbetter(ob, oi, best, best_idx)) { best = ob; best_idx = oi; best_c = make_float2(ocx, ocy); }
+                if (gbetter(obk, oi, best, best_idx)) { best = obk; best_idx = oi; best_c = make_float2(ocx, ocy); }
             }
-            if (lane == 0) { rk[warp] = best; ri[warp] = best_idx; rc[warp] = best_c; }
-            asm volatile("bar.sync 1, %0;" ::"n"(kTM) : "memory");
-            if (tid == 0) {
-                float b = rk[0];
-                long long bi = ri[0];
-                float2 bc = rc[0];
+            if (lane == 0) { rk[t][wq] = best; ri[t][wq] = best_idx; rc[t][wq] = best_c; }
+            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+            if (r == 0) {
+                float b = rk[t][0];
+                long long bi = ri[t][0];
+                float2 bc = rc[t][0];
                 for (int w = 1; w < 4; ++w)
-                    if (gbetter(rk[w], ri[w], b, bi)) { b = rk[w]; bi = ri[w]; bc = rc[w]; }
-                a.pkey[bx] = b;
-                a.pidx[bx] = (b >= 0.f) ? bi : -1;
-                if (a.pchi) a.pchi[bx] = bc;
-                if (a.pvmax) { a.pvmax[bx] = 0.f; a.psum[bx] = 0.f; }
+                    if (gbetter(rk[t][w], ri[t][w], b, bi)) { b = rk[t][w]; bi = ri[t][w]; bc = rc[t][w]; }
+                a.pkey[ob] = b;
+                a.pidx[ob] = (b >= 0.f) ? bi : -1;
+                if (a.pchi) a.pchi[ob] = bc;
+                if (a.pvmax) { a.pvmax[ob] = 0.f; a.psum[ob] = 0.f; }
             }
         }
         // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) in FP64 (SNRL, Eq. 38)
-        if (a.cdiag != nullptr && m == l && tile == 0 && ct == 0) {
+        if (a.cdiag != nullptr && tile == 0 && ct == 0) {
+            const bool diag = (m == l);
             double sr = 0.0, si = 0.0;
-            for (int n = tid; n < N; n += kTM) {
-                const float2 xv = xm[n], hv = hl[n];
-                const double xr = xv.x, xi = xv.y, hr = hv.x, hi_ = hv.y;
-                sr += xr * hr + xi * hi_;
-                si += xi * hr - xr * hi_;
+            if (diag) {
+                for (int n = r; n < N; n += kTM) {
+                    const float2 xv = xm[n], hv = hl[n];
+                    const double xr = xv.x, xi = xv.y, hr = hv.x, hi_ = hv.y;
+                    sr += xr * hr + xi * hi_;
+                    si += xi * hr - xr * hi_;
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
                 si += __shfl_xor_sync(0xffffffffu, si, o);
             }
-            if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
-            asm volatile("bar.sync 1, %0;" ::"n"(kTM) : "memory");
-            if (tid == 0)
-                a.cdiag[m] = make_double2(red[0][0] + red[0][1] + red[0][2] + red[0][3],
-                                          red[1][0] + red[1][1] + red[1][2] + red[1][3]);
+            if (lane == 0) { red[t][0][wq] = sr; red[t][1][wq] = si; }
+            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+            if (diag && r == 0)
+                a.cdiag[m] = make_double2(red[t][0][0] + red[t][0][1] + red[t][0][2] + red[t][0][3],
+                                          red[t][1][0] + red[t][1][1] + red[t][1][2] + red[t][1][3]);
         }
     }
 
-    __syncthreads();
-    if (warp == 4) {
+    tc::fence_before_sync();
+    if (C > 1) tc::cluster_sync();   // no CTA leaves while the cluster still addresses it
+    else __syncthreads();
+    if (warp == WMMA) {
         __syncwarp();
         tc::fence_after_sync();
         tc::tmem_dealloc(tbase, TCOLS);
@@ -359,28 +408,79 @@ int gemm_bins_per_tile(int L) {
     return lb;
 }
 
-// Dynamic shared memory of a CTA.  It is padded so that the CTAs that fit on
-// an SM never ask for more tensor memory than the SM's 512 columns (at most
-// two CTAs of 256 columns, one of 512), so no allocation has to wait.
-int gemm_smem_bytes(int L, int N) {
+// Dynamic shared memory of a CTA (0 if the shape does not fit).  It is padded
+// so that the CTAs that fit on an SM never ask for more tensor memory than the
+// SM's 512 columns, so no allocation has to wait.
+int gemm_smem_bytes(int L, int N, int spc, int stages, int tiles) {
     const int NC = 2 * gemm_bins_per_tile(L);
-    const int n_kc = (N + kSPC - 1) / kSPC;
-    const int need = kStages * NC * kKC * 4 + (int)sizeof(float2) * (2 * kSPC * n_kc + kTM);
-    const int floor_bytes = (gemm_tmem_cols(NC) == 512) ? 116 * 1024 : 77 * 1024;
-    return need > floor_bytes ? need : floor_bytes;
+    const int tcols = gemm_tmem_cols(NC, spc, stages, tiles);
+    if (tcols == 0 || spc <= 0 || tiles < 1) return 0;
+    const int n_kc = (N + spc - 1) / spc;
+    const int need = stages * NC * spc * 8 + tiles * (int)sizeof(float2) * (2 * spc * n_kc + kTM);
+    const int floor_bytes = 228 * 1024 / (512 / tcols + 1) + 1024;
+    const int b = need > floor_bytes ? need : floor_bytes;
+    return b <= 227 * 1024 ? b : 0;
+}
+
+template <int NC, int SPC, int ST, int T>
+static cudaError_t launch_cfg(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
+    if constexpr (gemm_tmem_cols(NC, SPC, ST, T) == 0) {
+        return cudaErrorInvalidValue;   // more tensor memory than an SM has
+    } else {
+    auto kern = fwd_gemm_kernel<NC, SPC, ST, T>;
+    cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
+    if (e != cudaSuccess || prepare_only) return e;
+    const int grid = g.f.M * g.f.M / T * g.f.n_chunks * g.n_ct;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32 * (4 * T + 2));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (g.csize > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = g.csize;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (g.f.pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, kern, g);
+    }
+}
+
+template <int NC, int T>
+static cudaError_t launch_nct(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
+    switch (g.spc * 16 + g.stages) {
+        case 32 * 16 + 2: return launch_cfg<NC, 32, 2, T>(g, smem, s, prepare_only);
+        case 32 * 16 + 4: return launch_cfg<NC, 32, 4, T>(g, smem, s, prepare_only);
+        case 16 * 16 + 4: return launch_cfg<NC, 16, 4, T>(g, smem, s, prepare_only);
+        case 16 * 16 + 6: return launch_cfg<NC, 16, 6, T>(g, smem, s, prepare_only);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int NC>
 static cudaError_t launch_nc(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
-    auto kern = fwd_gemm_kernel<NC>;
-    cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
-    if (e != cudaSuccess || prepare_only) return e;
-    const int grid = g.f.M * g.f.M * g.f.n_chunks * g.n_ct;
-    return launch_ex(kern, dim3(grid), dim3(kGThreads), smem, s, g.f.pdl != 0, g);
+    return g.tiles == 2 ? launch_nct<NC, 2>(g, smem, s, prepare_only) : launch_nct<NC, 1>(g, smem, s, prepare_only);
+}
+
+bool gemm_shape_supported(int L, int N, int spc, int stages, int tiles) {
+    const int key = spc * 16 + stages;
+    const bool listed = key == 32 * 16 + 2 || key == 32 * 16 + 4 || key == 16 * 16 + 4 || key == 16 * 16 + 6;
+    return listed && (tiles == 1 || tiles == 2) && gemm_smem_bytes(L, N, spc, stages, tiles) > 0;
 }
 
 static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only) {
-    const int smem = gemm_smem_bytes(g.f.L, g.f.N);
+    if (!gemm_shape_supported(g.f.L, g.f.N, g.spc, g.stages, g.tiles)) return cudaErrorInvalidValue;
+    const int smem = gemm_smem_bytes(g.f.L, g.f.N, g.spc, g.stages, g.tiles);
     switch (2 * gemm_bins_per_tile(g.f.L)) {
         case 32: return launch_nc<32>(g, smem, s, prepare_only);
         case 64: return launch_nc<64>(g, smem, s, prepare_only);
@@ -390,15 +490,21 @@ static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only
     }
 }
 
-cudaError_t gemm_prepare(int L, int N) {
+cudaError_t gemm_prepare(int L, int N, int spc, int stages, int tiles) {
     GemmArgs g{};
     g.f.L = L;
     g.f.N = N;
+    g.spc = spc;
+    g.stages = stages;
+    g.tiles = tiles;
     return dispatch(g, nullptr, true);
 }
 
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s) {
-    if (g.f.n_chunks * kTM < g.f.D || g.n_kc * kSPC < g.f.N) return cudaErrorInvalidValue;
+    if (g.f.n_chunks * kTM < g.f.D || g.spc <= 0 || g.n_kc * g.spc < g.f.N) return cudaErrorInvalidValue;
+    const int P = g.f.M * g.f.M;
+    if (!(g.tiles == 1 || g.tiles == 2) || P % g.tiles != 0) return cudaErrorInvalidValue;
+    if (!(g.csize == 1 || g.csize == 2 || g.csize == 4) || (P / g.tiles) % g.csize != 0) return cudaErrorInvalidValue;
     return dispatch(g, s, false);
 }
 

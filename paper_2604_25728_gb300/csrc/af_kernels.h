@@ -96,21 +96,24 @@ int dft_col_tiles(int L);
 cudaError_t launch_fwd_dft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
 cudaError_t launch_fwd_dft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
 
-// Narrow-window path on tcgen05 tensor cores: one CTA per 128 delays of a
-// pair and per column tile of LB bins (LB = gemm_bins_per_tile(L)); BF16
-// hi/lo split operands, FP32 accumulation in tensor memory.
+// Narrow-window path on tcgen05 tensor cores: one CTA per 128 delays of
+// `tiles` pairs and per column tile of LB bins (LB = gemm_bins_per_tile(L));
+// BF16 hi/lo split operands, FP32 accumulation in tensor memory.
 constexpr int kGemmRows = 128;      // delays per tile (MMA M)
-constexpr int kGemmSamples = 32;    // samples per pipeline stage
 struct GemmArgs {
     FwdArgs<float2, float> f;   // x, h, wmap, mode, pkey/pidx/pchi, cdiag, chi_out, ctr_inc, pdl
-    const void* bimg;           // [n_ct][n_kc][hi | lo][2 LB x 64] BF16 images of E (gemm_build_image)
+    const void* bimg;           // [n_ct][n_kc][hi | lo][2 LB x 2 spc] BF16 images of E
     int* err;                   // bit 1 set when a pipeline wait timed out
     int n_ct;                   // column tiles = ceil(L / LB)
-    int n_kc;                   // sample chunks = ceil(N / 32)
+    int n_kc;                   // sample chunks = ceil(N / spc)
+    int spc, stages;            // samples per pipeline stage, stages
+    int tiles;                  // pairs (delay tiles) per CTA sharing each B stage (1, or 2 when M*M is even)
+    int csize;                  // CTAs per cluster sharing each B stage (1, 2 or 4; divides M*M / tiles)
 };
 int gemm_bins_per_tile(int L);
-int gemm_smem_bytes(int L, int N);
-cudaError_t gemm_prepare(int L, int N);
+int gemm_smem_bytes(int L, int N, int spc, int stages, int tiles);
+bool gemm_shape_supported(int L, int N, int spc, int stages, int tiles);
+cudaError_t gemm_prepare(int L, int N, int spc, int stages, int tiles);
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
 
 struct QuantArgs;

@@ -40,16 +40,16 @@ inline float bf16_float(uint16_t b) {
 }
 
 // Images of the real-embedded DFT matrix for the tensor-core path, one per
-// (column tile, chunk of 32 samples), each [hi | lo] of 2 LB rows x 64 K in
-// the canonical K-major no-swizzle layout: 8x8 BF16 core matrices, 128 B
-// apart along K, 8 core matrices (1 KB) apart between row groups.  Row
+// (column tile, chunk of SPC samples), each [hi | lo] of 2 LB rows x 2 SPC K
+// in the canonical K-major no-swizzle layout: 8x8 BF16 core matrices, 128 B
+// apart along K, 2 SPC / 8 core matrices apart between row groups.  Row
 // 2j + u is output bin j (u = 0 real, 1 imaginary part), K index 2s + t is
 // sample s of the chunk (t = 0 real, 1 imaginary part of the lag product):
 //   (t,u) = (0,0): cos, (1,0): -sin, (0,1): sin, (1,1): cos  of 2 pi nu_j n.
 // Each value v (built in FP64) is stored as hi = bf16(v), lo = bf16(v - hi).
-void gemm_build_image(const std::vector<double>& nu, int N, std::vector<uint16_t>& img) {
+void gemm_build_image(const std::vector<double>& nu, int N, int SPC, std::vector<uint16_t>& img) {
     const int L = (int)nu.size();
-    const int LB = af::gemm_bins_per_tile(L), NC = 2 * LB, SPC = af::kGemmSamples, KC = 2 * SPC;
+    const int LB = af::gemm_bins_per_tile(L), NC = 2 * LB, KC = 2 * SPC;
     const int n_ct = (L + LB - 1) / LB, n_kc = (N + SPC - 1) / SPC;
     const size_t part = (size_t)NC * KC;
     img.assign((size_t)n_ct * n_kc * 2 * part, 0);
@@ -118,6 +118,9 @@ struct af_ctx {
     float2* E = nullptr;       // [N][L] e^{j 2 pi nu_j n} (DFT path)
     uint16_t* bimg = nullptr;  // BF16 hi/lo images of E (tensor-core path)
     int gemm_n_ct = 0, gemm_n_kc = 0;
+    int gemm_spc = 32, gemm_stages = 2;   // samples per pipeline stage, stages
+    int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
+    int gemm_csize = 1;                   // CTAs per cluster sharing each B stage
     double2* pre64 = nullptr;
     double2* tw64 = nullptr;
     double2* E64 = nullptr;
@@ -322,9 +325,26 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         return fail(AF_ERR_UNIMPLEMENTED);
     }
     c->path = (cfg->path == AF_PATH_AUTO) ? (uniform ? AF_PATH_FFT : AF_PATH_DFT) : cfg->path;
-    if (c->path == AF_PATH_SPLIT_BF16 && gemm_smem_bytes(L, N) > 227 * 1024) {
-        c->err = "AF_PATH_SPLIT_BF16: N too large for the shared-memory staging";
-        return fail(AF_ERR_UNIMPLEMENTED);
+    if (c->path == AF_PATH_SPLIT_BF16) {
+        if (const char* e = getenv("SQNGD_GEMM_CFG")) {   // "<samples per stage>x<stages>"
+            int a = 0, b = 0;
+            if (sscanf(e, "%dx%d", &a, &b) == 2) { c->gemm_spc = a; c->gemm_stages = b; }
+        }
+        const int P = M * M;
+        c->gemm_tiles = 1;
+        c->gemm_csize = 1;
+        if (const char* e = getenv("SQNGD_GEMM_TILES")) {
+            const int v = atoi(e);
+            if ((v == 1 || v == 2) && P % v == 0) c->gemm_tiles = v;
+        }
+        if (const char* e = getenv("SQNGD_GEMM_CLUSTER")) {
+            const int v = atoi(e);
+            if ((v == 1 || v == 2 || v == 4) && (P / c->gemm_tiles) % v == 0) c->gemm_csize = v;
+        }
+        if (!gemm_shape_supported(L, N, c->gemm_spc, c->gemm_stages, c->gemm_tiles)) {
+            c->err = "AF_PATH_SPLIT_BF16: pipeline shape does not fit this N and L";
+            return fail(AF_ERR_UNIMPLEMENTED);
+        }
     }
     c->grid_fft = uniform;
     if (cfg->pnorm > 0.0) {
@@ -404,11 +424,11 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     }
     if (c->path == AF_PATH_SPLIT_BF16) {
         std::vector<uint16_t> img;
-        gemm_build_image(c->nu, N, img);
+        gemm_build_image(c->nu, N, c->gemm_spc, img);
         if ((s = upload(c, &c->bimg, img))) return fail(s);
         const int LB = gemm_bins_per_tile(L);
         c->gemm_n_ct = (L + LB - 1) / LB;
-        c->gemm_n_kc = (N + kGemmSamples - 1) / kGemmSamples;
+        c->gemm_n_kc = (N + c->gemm_spc - 1) / c->gemm_spc;
     }
     if (cfg->weights) {
         c->wmap_host.assign(cfg->weights, cfg->weights + (size_t)c->D * L);
@@ -423,7 +443,8 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     // kernels' shared-memory limits are raised here, outside any graph capture
     {
         cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e)
-                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N) : dft_prepare_f32(N);
+                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N, c->gemm_spc, c->gemm_stages, c->gemm_tiles)
+                        : dft_prepare_f32(N);
         if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
         if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
         if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
@@ -555,6 +576,10 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
         g.err = c->errflag;
         g.n_ct = c->gemm_n_ct;
         g.n_kc = c->gemm_n_kc;
+        g.spc = c->gemm_spc;
+        g.stages = c->gemm_stages;
+        g.tiles = c->gemm_tiles;
+        g.csize = c->gemm_csize;
         return launch_fwd_gemm(g, s);
     }
     return (c->path == AF_PATH_FFT) ? launch_fwd_fft_f32(a, s) : launch_fwd_dft_f32(a, s);

@@ -170,3 +170,20 @@ def test_split_full_size_precision(api, orc):
     ref = orc.ambiguity_cells(x, h, w.nu, w.k_lo, w.k_hi, cells)
     assert np.max(np.abs(got - ref)) <= CHI_TOL * w.N
     _check_terms(orc, ctx, x, h, w.nu, w.k_lo, w.k_hi, w.eps, w.snrl_db)
+
+
+@pytest.mark.parametrize("shape", [("16x4", "1", "1"), ("32x2", "2", "1"), ("16x4", "2", "2"), ("32x2", "1", "4")])
+def test_split_pipeline_variants(api, orc, shape, monkeypatch):
+    """Other pipeline shapes of the tensor-core kernel (samples per stage x
+    stages, pairs per CTA, CTAs per multicast cluster) give the same chi."""
+    cfg, tiles, cluster = shape
+    monkeypatch.setenv("SQNGD_GEMM_CFG", cfg)
+    monkeypatch.setenv("SQNGD_GEMM_TILES", tiles)
+    monkeypatch.setenv("SQNGD_GEMM_CLUSTER", cluster)
+    M, N, nu, k_lo, k_hi = 4, 300, wl.window_grid(0.1, 40), -299, 299
+    x, h = _pair(orc, 700 + N, M, N)
+    ctx = _ctx(api, M, N, 4, nu, k_lo, k_hi, eps=0.2, snrl_db=1.0)
+    chi = ctx.af_ambiguity(_dev(x), _dev(h)).cpu().numpy()
+    ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
+    assert np.max(np.abs(chi - ref)) <= CHI_TOL * np.max(np.abs(ref))
+    _check_terms(orc, ctx, x, h, nu, k_lo, k_hi, 0.2, 1.0)
