@@ -43,6 +43,9 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--fwd-path", default="fft", choices=["fft", "split"],
+                   help="with --fwd-only: fft = the mid workload on the FFT path, split = the narrow-window "
+                        "workload on the tensor-core path")
     p.add_argument("--fwd-only", type=int, default=0,
                    help="run only N launches of the fused forward pass on the workload (for profiler captures)")
     return p.parse_args()
@@ -277,6 +280,15 @@ def run_ours(args):
 
     w = _workload()
     seed = rank_seed(rank)
+    if args.fwd_only > 0 and args.fwd_path == "split":
+        w = wl.precision()
+        ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, path=api.AF_PATH_SPLIT_BF16)
+        x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
+        for _ in range(args.fwd_only):
+            ctx.af_forward(x, x)
+        ctx.af_sync()
+        ctx.close()
+        return
     ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
                       n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x)
     stream = torch.cuda.current_stream()

@@ -41,12 +41,14 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 // Wait for phase `parity` of `bar`.  Gives up when another role has
-// aborted (unless `drain`) or after kTimeoutNs, which aborts the CTA.
-__device__ __noinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err, bool drain) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
+// aborted (unless `drain`) or after kTimeoutNs, which aborts the CTA.  The
+// abort flag and the clock are looked at every 64 polls only.
+__device__ __noinline__ bool gwait_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                        bool drain) {
     const unsigned long long t0 = gtimer();
     for (;;) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
+        for (int k = 0; k < 64; ++k)
+            if (tc::mbar_try_wait(bar, parity)) return true;
         if (!drain && *abort_flag) return false;
         if (gtimer() - t0 > kTimeoutNs) {
             *abort_flag = 1;
@@ -54,6 +56,11 @@ __device__ __noinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int*
             return false;
         }
     }
+}
+__device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                      bool drain) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    return gwait_slow(bar, parity, abort_flag, err, drain);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
@@ -100,15 +107,18 @@ __device__ __forceinline__ bool gbetter(float a, long long ia, float b, long lon
     return a > b || (a == b && ia < ib);
 }
 
-// Tensor-memory columns of a CTA: T accumulators of NC columns plus ST A
+// Tensor-memory columns of a CTA: T accumulators of NC columns plus SA A
 // stages of T tiles x (SPC hi + SPC lo) columns, rounded up to a power of
 // two (0 if more than 512).
-__host__ __device__ constexpr int gemm_tmem_cols(int NC, int SPC, int ST, int T) {
-    return (T * NC + 2 * SPC * ST * T <= 128) ? 128 : (T * NC + 2 * SPC * ST * T <= 256) ? 256
-         : (T * NC + 2 * SPC * ST * T <= 512) ? 512 : 0;
+__host__ __device__ constexpr int gemm_tmem_cols(int NC, int SPC, int SA, int T) {
+    return (T * NC + 2 * SPC * SA * T <= 128) ? 128 : (T * NC + 2 * SPC * SA * T <= 256) ? 256
+         : (T * NC + 2 * SPC * SA * T <= 512) ? 512 : 0;
 }
 
-template <int NC, int kSPC, int kStages, int T>
+// kSB stages of B images in shared memory (filled by bulk copies), kSA
+// stages of lag products in tensor memory (filled by tcgen05.st); chunk i
+// uses B stage i % kSB and A stage i % kSA.
+template <int NC, int kSPC, int kSB, int kSA, int T>
 __global__ void __launch_bounds__(32 * (4 * T + 2), 1)
 fwd_gemm_kernel(const GemmArgs g) {
     const FwdArgs<float2, float>& a = g.f;
@@ -117,16 +127,16 @@ fwd_gemm_kernel(const GemmArgs g) {
     constexpr int NPROD = kTM * T;                   // producer / epilogue threads
     constexpr int WMMA = 4 * T, WLOAD = 4 * T + 1;   // MMA and loader warps
     constexpr int STAGE_BYTES = NC * kKC * 2 * 2;    // hi | lo images
-    constexpr int TCOLS = gemm_tmem_cols(NC, kSPC, kStages, T);
+    constexpr int TCOLS = gemm_tmem_cols(NC, kSPC, kSA, T);
     static_assert(NC % 32 == 0 && NC >= 32 && NC <= 256, "column tile");
     static_assert(TCOLS > 0 && kSPC % 8 == 0, "stage shape");
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* bst = smem_raw;                                        // [kStages][STAGE_BYTES]
+    unsigned char* bst = smem_raw;                                        // [kSB][STAGE_BYTES]
     const int XH = 2 * kSPC * g.n_kc + kTM;                               // per tile: xs, then hs
-    float2* xh_base = reinterpret_cast<float2*>(smem_raw + kStages * STAGE_BYTES);
+    float2* xh_base = reinterpret_cast<float2*>(smem_raw + kSB * STAGE_BYTES);
 
-    __shared__ __align__(8) uint64_t bfull[kStages], afull[kStages], empty[kStages], accfull;
+    __shared__ __align__(8) uint64_t bfull[kSB], bempty[kSB], afull[kSA], aempty[kSA], accfull;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ float rk[T][4];
@@ -159,10 +169,13 @@ fwd_gemm_kernel(const GemmArgs g) {
     const int SLB = STAGE_BYTES / C;                           // this CTA's slice of every stage
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kSB; ++s) {
             tc::mbar_init(&bfull[s], 1);
-            tc::mbar_init(&afull[s], NPROD);
-            tc::mbar_init(&empty[s], C);   // one MMA commit from every CTA of the cluster
+            tc::mbar_init(&bempty[s], C);   // one MMA commit from every CTA of the cluster
+        }
+        for (int s = 0; s < kSA; ++s) {
+            tc::mbar_init(&afull[s], NPROD / 32);   // one arrival per producer warp
+            tc::mbar_init(&aempty[s], 1);
         }
         tc::mbar_init(&accfull, 1);
         s_abort = 0;
@@ -199,26 +212,26 @@ fwd_gemm_kernel(const GemmArgs g) {
         if (lane == 0) {
             // the tables are constant: the first stages load before the
             // previous kernel in the stream has finished
-            const int pro = min(kStages, nch);
+            const int pro = min(kSB, nch);
             for (int i = 0; i < pro; ++i) issue(i, i);
             issued = pro;
         }
         pdl_wait();
         pdl_trigger();
         if (lane == 0) {
-            for (int i = kStages; i < nch; ++i) {
-                const int s = i % kStages;
+            for (int i = kSB; i < nch; ++i) {
+                const int s = i % kSB;
                 // every CTA of the cluster has finished with stage s
-                if (!gwait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, g.err, false)) break;
+                if (!gwait(&bempty[s], ((i / kSB) - 1) & 1, abort_flag, g.err, false)) break;
                 issue(i, s);
                 issued = i + 1;
             }
             // every stage this CTA expects has landed, and every MMA commit
             // the cluster sends to this CTA has arrived, before it exits
-            for (int i = max(0, issued - kStages); i < issued; ++i)
-                gwait(&bfull[i % kStages], (i / kStages) & 1, abort_flag, g.err, true);
-            for (int i = max(0, nch - kStages); i < nch; ++i)
-                gwait(&empty[i % kStages], (i / kStages) & 1, abort_flag, g.err, true);
+            for (int i = max(0, issued - kSB); i < issued; ++i)
+                gwait(&bfull[i % kSB], (i / kSB) & 1, abort_flag, g.err, true);
+            for (int i = max(0, nch - kSB); i < nch; ++i)
+                gwait(&bempty[i % kSB], (i / kSB) & 1, abort_flag, g.err, true);
         }
     } else if (warp == WMMA) {
         // ------------------------------------------------- MMA issuer --
@@ -226,31 +239,33 @@ fwd_gemm_kernel(const GemmArgs g) {
         pdl_trigger();
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16(kTM, NC);
-            const uint32_t bsm = tc::smem_u32(bst);
+            // Descriptors of stage 0; a stage, a K step and the lo image are
+            // constant offsets in the start-address field (address >> 4,
+            // bits 0-13), so the issue loop is a few adds per MMA.
+            const uint64_t dbase = tc::smem_desc(tc::smem_u32(bst), 128, (kKC / 8) * 128);
+            constexpr uint64_t kStageStep = STAGE_BYTES >> 4, kLoStep = (NC * kKC * 2) >> 4, kKStep = 256 >> 4;
             for (int i = 0; i < nch; ++i) {
-                const int s = i % kStages;
-                const uint32_t ph = (i / kStages) & 1;
-                if (!gwait(&bfull[s], ph, abort_flag, g.err, false)) break;
-                if (!gwait(&afull[s], ph, abort_flag, g.err, false)) break;
+                const int s = i % kSB, sa = i % kSA;
+                if (!gwait(&bfull[s], (i / kSB) & 1, abort_flag, g.err, false)) break;
+                if (!gwait(&afull[sa], (i / kSA) & 1, abort_flag, g.err, false)) break;
                 tc::fence_after_sync();
-                const uint32_t b_hi = bsm + s * STAGE_BYTES;
-                const uint32_t b_lo = b_hi + NC * kKC * 2;
+                const uint64_t dh = dbase + (uint64_t)s * kStageStep;
+                const uint64_t dl = dh + kLoStep;
+                const uint32_t acc0 = (i > 0) ? 1u : 0u;
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
                     const uint32_t d_t = tbase + t * NC;
-                    const uint32_t a_hi = tbase + T * NC + (s * T + t) * kKC;
-                    const uint32_t a_lo = a_hi + kSPC;
+                    const uint32_t a_hi = tbase + T * NC + (sa * T + t) * kKC;
 #pragma unroll
                     for (int q = 0; q < kKC / 16; ++q) {
-                        const uint64_t dh = tc::smem_desc(b_hi + q * 256, 128, (kKC / 8) * 128);
-                        const uint64_t dl = tc::smem_desc(b_lo + q * 256, 128, (kKC / 8) * 128);
-                        mma_ts(d_t, a_hi + 8 * q, dh, idesc, (i > 0 || q > 0) ? 1u : 0u);
-                        mma_ts(d_t, a_hi + 8 * q, dl, idesc, 1u);
-                        mma_ts(d_t, a_lo + 8 * q, dh, idesc, 1u);
+                        mma_ts(d_t, a_hi + 8 * q, dh + q * kKStep, idesc, q == 0 ? acc0 : 1u);
+                        mma_ts(d_t, a_hi + 8 * q, dl + q * kKStep, idesc, 1u);
+                        mma_ts(d_t, a_hi + kSPC + 8 * q, dh + q * kKStep, idesc, 1u);
                     }
                 }
-                if (C > 1) tc::mma_commit_mc(&empty[s], cmask);
-                else tc::mma_commit(&empty[s]);
+                if (C > 1) tc::mma_commit_mc(&bempty[s], cmask);
+                else tc::mma_commit(&bempty[s]);
+                tc::mma_commit(&aempty[sa]);
             }
             tc::mma_commit(&accfull);
             gwait(&accfull, 0, abort_flag, g.err, true);
@@ -269,13 +284,55 @@ fwd_gemm_kernel(const GemmArgs g) {
         const float2* xm = a.x + (size_t)m * N;
         const float2* hl = a.h + (size_t)l * N;
         const int nx = kSPC * nch, nh = kSPC * nch + kTM;
-        for (int i = r; i < nh; i += kTM) {
-            const int p = kSPC * c0 + k_first + i;
-            hs[i] = (p >= 0 && p < N) ? hl[p] : make_float2(0.f, 0.f);
-            if (i < nx) {
-                const int n = kSPC * c0 + i;
-                xs[i] = (n < N) ? xm[n] : make_float2(0.f, 0.f);
+        // all loads of a batch are in flight before the first store
+        constexpr int FB = 8;
+        for (int i0 = r; i0 < nh; i0 += kTM * FB) {
+            float2 hv[FB], xv[FB];
+#pragma unroll
+            for (int q = 0; q < FB; ++q) {
+                const int i = i0 + q * kTM;
+                const int p = kSPC * c0 + k_first + i, n = kSPC * c0 + i;
+                hv[q] = (i < nh && p >= 0 && p < N) ? hl[p] : make_float2(0.f, 0.f);
+                xv[q] = (i < nx && n < N) ? xm[n] : make_float2(0.f, 0.f);
             }
+#pragma unroll
+            for (int q = 0; q < FB; ++q) {
+                const int i = i0 + q * kTM;
+                if (i < nh) hs[i] = hv[q];
+                if (i < nx) xs[i] = xv[q];
+            }
+        }
+        // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) in FP64 (SNRL, Eq. 38), while
+        // the first B stages are still in flight
+        if (a.cdiag != nullptr && tile == 0 && ct == 0) {
+            const bool diag = (m == l);
+            double sr = 0.0, si = 0.0;
+            if (diag) {
+                for (int n0 = r; n0 < N; n0 += kTM * FB) {
+                    float2 xv[FB], hv[FB];
+#pragma unroll
+                    for (int q = 0; q < FB; ++q) {
+                        const int n = n0 + q * kTM;
+                        xv[q] = n < N ? xm[n] : make_float2(0.f, 0.f);
+                        hv[q] = n < N ? hl[n] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < FB; ++q) {
+                        const double xr = xv[q].x, xi = xv[q].y, hr = hv[q].x, hi_ = hv[q].y;
+                        sr += xr * hr + xi * hi_;
+                        si += xi * hr - xr * hi_;
+                    }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+            }
+            if (lane == 0) { red[t][0][warp & 3] = sr; red[t][1][warp & 3] = si; }
+            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+            if (diag && r == 0)
+                a.cdiag[m] = make_double2(red[t][0][0] + red[t][0][1] + red[t][0][2] + red[t][0][3],
+                                          red[t][1][0] + red[t][1][1] + red[t][1][2] + red[t][1][3]);
         }
         asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
 
@@ -283,11 +340,13 @@ fwd_gemm_kernel(const GemmArgs g) {
         const uint32_t trow = tbase + ((uint32_t)(wq * 32) << 16);
         bool ok = true;
         for (int i = 0; i < nch; ++i) {
-            const int s = i % kStages;
-            if (i >= kStages) {
-                // the warp agrees before its aligned tensor-memory stores
-                const bool w = gwait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, g.err, false);
-                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+            const int s = i % kSA;
+            if (i >= kSA) {
+                // one lane polls; the warp takes its verdict before the
+                // aligned tensor-memory stores
+                bool w = true;
+                if (lane == 0) w = gwait(&aempty[s], ((i / kSA) - 1) & 1, abort_flag, g.err, false);
+                if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
                 tc::fence_after_sync();
             }
             uint32_t hi[kSPC], lo[kSPC];
@@ -307,25 +366,53 @@ fwd_gemm_kernel(const GemmArgs g) {
             tmem_st<kSPC>(acol + kSPC, lo);
             tmem_st_wait();
             tc::fence_before_sync();
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&afull[s])) : "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&afull[s])) : "memory");
         }
 
         // ---- epilogue: accumulator -> sidelobe reduction (Eqs. 7-9) ----
         float best = -1.f;
         long long best_idx = 0x7fffffffffffffffLL;
         float2 best_c = make_float2(0.f, 0.f);
-        const bool acc_ready = ok && gwait(&accfull, 0, abort_flag, g.err, false);
-        if (__all_sync(0xffffffffu, acc_ready)) {
+        bool acc_ready = ok;
+        if (lane == 0 && ok) acc_ready = gwait(&accfull, 0, abort_flag, g.err, false);
+        if (__shfl_sync(0xffffffffu, acc_ready, 0)) {
             tc::fence_after_sync();
             const int d = d0 + r;
             const int k = a.k_lo + d;
             const bool row_ok = d < D && !(m == l && k == 0);
             const bool dump = a.mode == FWD_DUMP;
+            const bool fast = !dump && a.weight_mode == WM_UNIFORM;
 #pragma unroll 1
             for (int cc = 0; cc < NC / 32; ++cc) {
                 float v[32];
                 tc::tmem_ld32(trow + t * NC + cc * 32, v);
                 tc::tmem_ld_wait();
+                if (fast) {
+                    // cells of a row are visited in increasing index order, so
+                    // a group only matters if its largest key beats the best so
+                    // far, and then its first maximal cell is the candidate
+                    float key[16];
+                    const int jb = ct * LB + cc * 16;
+#pragma unroll
+                    for (int b = 0; b < 16; ++b)
+                        key[b] = (row_ok && jb + b < L) ? fmaf(v[2 * b], v[2 * b], v[2 * b + 1] * v[2 * b + 1]) : -1.f;
+                    float gm = key[0];
+#pragma unroll
+                    for (int b = 1; b < 16; ++b) gm = fmaxf(gm, key[b]);
+                    if (gm > best) {
+                        int bsel = 15;
+                        float cx = v[30], cy = v[31];
+#pragma unroll
+                        for (int b = 14; b >= 0; --b)
+                            if (key[b] == gm) { bsel = b; cx = v[2 * b]; cy = v[2 * b + 1]; }
+                        best = gm;
+                        best_idx = ((long long)pair * D + d) * L + jb + bsel;
+                        best_c = make_float2(cx, cy);
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int b = 0; b < 16; ++b) {
                     const int jj = ct * LB + cc * 16 + b;
@@ -368,28 +455,6 @@ fwd_gemm_kernel(const GemmArgs g) {
                 if (a.pvmax) { a.pvmax[ob] = 0.f; a.psum[ob] = 0.f; }
             }
         }
-        // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) in FP64 (SNRL, Eq. 38)
-        if (a.cdiag != nullptr && tile == 0 && ct == 0) {
-            const bool diag = (m == l);
-            double sr = 0.0, si = 0.0;
-            if (diag) {
-                for (int n = r; n < N; n += kTM) {
-                    const float2 xv = xm[n], hv = hl[n];
-                    const double xr = xv.x, xi = xv.y, hr = hv.x, hi_ = hv.y;
-                    sr += xr * hr + xi * hi_;
-                    si += xi * hr - xr * hi_;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                si += __shfl_xor_sync(0xffffffffu, si, o);
-            }
-            if (lane == 0) { red[t][0][wq] = sr; red[t][1][wq] = si; }
-            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
-            if (diag && r == 0)
-                a.cdiag[m] = make_double2(red[t][0][0] + red[t][0][1] + red[t][0][2] + red[t][0][3],
-                                          red[t][1][0] + red[t][1][1] + red[t][1][2] + red[t][1][3]);
-        }
     }
 
     tc::fence_before_sync();
@@ -411,23 +476,23 @@ int gemm_bins_per_tile(int L) {
 // Dynamic shared memory of a CTA (0 if the shape does not fit).  It is padded
 // so that the CTAs that fit on an SM never ask for more tensor memory than the
 // SM's 512 columns, so no allocation has to wait.
-int gemm_smem_bytes(int L, int N, int spc, int stages, int tiles) {
+int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles) {
     const int NC = 2 * gemm_bins_per_tile(L);
-    const int tcols = gemm_tmem_cols(NC, spc, stages, tiles);
+    const int tcols = gemm_tmem_cols(NC, spc, sa, tiles);
     if (tcols == 0 || spc <= 0 || tiles < 1) return 0;
     const int n_kc = (N + spc - 1) / spc;
-    const int need = stages * NC * spc * 8 + tiles * (int)sizeof(float2) * (2 * spc * n_kc + kTM);
+    const int need = sb * NC * spc * 8 + tiles * (int)sizeof(float2) * (2 * spc * n_kc + kTM);
     const int floor_bytes = 228 * 1024 / (512 / tcols + 1) + 1024;
     const int b = need > floor_bytes ? need : floor_bytes;
     return b <= 227 * 1024 ? b : 0;
 }
 
-template <int NC, int SPC, int ST, int T>
+template <int NC, int SPC, int SB, int SA, int T>
 static cudaError_t launch_cfg(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
-    if constexpr (gemm_tmem_cols(NC, SPC, ST, T) == 0) {
+    if constexpr (gemm_tmem_cols(NC, SPC, SA, T) == 0) {
         return cudaErrorInvalidValue;   // more tensor memory than an SM has
     } else {
-    auto kern = fwd_gemm_kernel<NC, SPC, ST, T>;
+    auto kern = fwd_gemm_kernel<NC, SPC, SB, SA, T>;
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess || prepare_only) return e;
     const int grid = g.f.M * g.f.M / T * g.f.n_chunks * g.n_ct;
@@ -456,15 +521,16 @@ static cudaError_t launch_cfg(const GemmArgs& g, int smem, cudaStream_t s, bool 
     }
 }
 
+// Pipeline shapes built: samples per stage x B stages x A stages.
+#define AF_GEMM_SHAPES(X) X(32, 2, 2) X(32, 4, 2) X(16, 4, 2) X(16, 8, 4)
+
 template <int NC, int T>
 static cudaError_t launch_nct(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
-    switch (g.spc * 16 + g.stages) {
-        case 32 * 16 + 2: return launch_cfg<NC, 32, 2, T>(g, smem, s, prepare_only);
-        case 32 * 16 + 4: return launch_cfg<NC, 32, 4, T>(g, smem, s, prepare_only);
-        case 16 * 16 + 4: return launch_cfg<NC, 16, 4, T>(g, smem, s, prepare_only);
-        case 16 * 16 + 6: return launch_cfg<NC, 16, 6, T>(g, smem, s, prepare_only);
-        default: return cudaErrorInvalidValue;
-    }
+#define AF_GEMM_CASE(P, B, A) \
+    if (g.spc == P && g.sb == B && g.sa == A) return launch_cfg<NC, P, B, A, T>(g, smem, s, prepare_only);
+    AF_GEMM_SHAPES(AF_GEMM_CASE)
+#undef AF_GEMM_CASE
+    return cudaErrorInvalidValue;
 }
 
 template <int NC>
@@ -472,15 +538,17 @@ static cudaError_t launch_nc(const GemmArgs& g, int smem, cudaStream_t s, bool p
     return g.tiles == 2 ? launch_nct<NC, 2>(g, smem, s, prepare_only) : launch_nct<NC, 1>(g, smem, s, prepare_only);
 }
 
-bool gemm_shape_supported(int L, int N, int spc, int stages, int tiles) {
-    const int key = spc * 16 + stages;
-    const bool listed = key == 32 * 16 + 2 || key == 32 * 16 + 4 || key == 16 * 16 + 4 || key == 16 * 16 + 6;
-    return listed && (tiles == 1 || tiles == 2) && gemm_smem_bytes(L, N, spc, stages, tiles) > 0;
+bool gemm_shape_supported(int L, int N, int spc, int sb, int sa, int tiles) {
+    bool listed = false;
+#define AF_GEMM_LISTED(P, B, A) listed = listed || (spc == P && sb == B && sa == A);
+    AF_GEMM_SHAPES(AF_GEMM_LISTED)
+#undef AF_GEMM_LISTED
+    return listed && (tiles == 1 || tiles == 2) && gemm_smem_bytes(L, N, spc, sb, sa, tiles) > 0;
 }
 
 static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only) {
-    if (!gemm_shape_supported(g.f.L, g.f.N, g.spc, g.stages, g.tiles)) return cudaErrorInvalidValue;
-    const int smem = gemm_smem_bytes(g.f.L, g.f.N, g.spc, g.stages, g.tiles);
+    if (!gemm_shape_supported(g.f.L, g.f.N, g.spc, g.sb, g.sa, g.tiles)) return cudaErrorInvalidValue;
+    const int smem = gemm_smem_bytes(g.f.L, g.f.N, g.spc, g.sb, g.sa, g.tiles);
     switch (2 * gemm_bins_per_tile(g.f.L)) {
         case 32: return launch_nc<32>(g, smem, s, prepare_only);
         case 64: return launch_nc<64>(g, smem, s, prepare_only);
@@ -490,12 +558,13 @@ static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only
     }
 }
 
-cudaError_t gemm_prepare(int L, int N, int spc, int stages, int tiles) {
+cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles) {
     GemmArgs g{};
     g.f.L = L;
     g.f.N = N;
     g.spc = spc;
-    g.stages = stages;
+    g.sb = sb;
+    g.sa = sa;
     g.tiles = tiles;
     return dispatch(g, nullptr, true);
 }

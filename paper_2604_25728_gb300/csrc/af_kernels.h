@@ -106,14 +106,15 @@ struct GemmArgs {
     int* err;                   // bit 1 set when a pipeline wait timed out
     int n_ct;                   // column tiles = ceil(L / LB)
     int n_kc;                   // sample chunks = ceil(N / spc)
-    int spc, stages;            // samples per pipeline stage, stages
+    int spc;                    // samples per pipeline stage
+    int sb, sa;                 // stages of B images (shared memory) and of lag products (tensor memory)
     int tiles;                  // pairs (delay tiles) per CTA sharing each B stage (1, or 2 when M*M is even)
     int csize;                  // CTAs per cluster sharing each B stage (1, 2 or 4; divides M*M / tiles)
 };
 int gemm_bins_per_tile(int L);
-int gemm_smem_bytes(int L, int N, int spc, int stages, int tiles);
-bool gemm_shape_supported(int L, int N, int spc, int stages, int tiles);
-cudaError_t gemm_prepare(int L, int N, int spc, int stages, int tiles);
+int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles);
+bool gemm_shape_supported(int L, int N, int spc, int sb, int sa, int tiles);
+cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles);
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
 
 struct QuantArgs;

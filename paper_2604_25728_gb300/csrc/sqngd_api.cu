@@ -118,7 +118,7 @@ struct af_ctx {
     float2* E = nullptr;       // [N][L] e^{j 2 pi nu_j n} (DFT path)
     uint16_t* bimg = nullptr;  // BF16 hi/lo images of E (tensor-core path)
     int gemm_n_ct = 0, gemm_n_kc = 0;
-    int gemm_spc = 32, gemm_stages = 2;   // samples per pipeline stage, stages
+    int gemm_spc = 32, gemm_sb = 2, gemm_sa = 2;   // samples per stage, B stages, A stages
     int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
     int gemm_csize = 1;                   // CTAs per cluster sharing each B stage
     double2* pre64 = nullptr;
@@ -326,9 +326,13 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     }
     c->path = (cfg->path == AF_PATH_AUTO) ? (uniform ? AF_PATH_FFT : AF_PATH_DFT) : cfg->path;
     if (c->path == AF_PATH_SPLIT_BF16) {
-        if (const char* e = getenv("SQNGD_GEMM_CFG")) {   // "<samples per stage>x<stages>"
-            int a = 0, b = 0;
-            if (sscanf(e, "%dx%d", &a, &b) == 2) { c->gemm_spc = a; c->gemm_stages = b; }
+        if (const char* e = getenv("SQNGD_GEMM_CFG")) {   // "<samples per stage>x<B stages>x<A stages>"
+            int a = 0, b = 0, d = 0;
+            if (sscanf(e, "%dx%dx%d", &a, &b, &d) != 3) {
+                c->err = "SQNGD_GEMM_CFG must read <samples per stage>x<B stages>x<A stages>";
+                return fail(AF_ERR_INVALID_ARG);
+            }
+            c->gemm_spc = a; c->gemm_sb = b; c->gemm_sa = d;
         }
         const int P = M * M;
         c->gemm_tiles = 1;
@@ -341,7 +345,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
             const int v = atoi(e);
             if ((v == 1 || v == 2 || v == 4) && (P / c->gemm_tiles) % v == 0) c->gemm_csize = v;
         }
-        if (!gemm_shape_supported(L, N, c->gemm_spc, c->gemm_stages, c->gemm_tiles)) {
+        if (!gemm_shape_supported(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)) {
             c->err = "AF_PATH_SPLIT_BF16: pipeline shape does not fit this N and L";
             return fail(AF_ERR_UNIMPLEMENTED);
         }
@@ -443,7 +447,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     // kernels' shared-memory limits are raised here, outside any graph capture
     {
         cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e)
-                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N, c->gemm_spc, c->gemm_stages, c->gemm_tiles)
+                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)
                         : dft_prepare_f32(N);
         if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
         if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
@@ -577,7 +581,8 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
         g.n_ct = c->gemm_n_ct;
         g.n_kc = c->gemm_n_kc;
         g.spc = c->gemm_spc;
-        g.stages = c->gemm_stages;
+        g.sb = c->gemm_sb;
+        g.sa = c->gemm_sa;
         g.tiles = c->gemm_tiles;
         g.csize = c->gemm_csize;
         return launch_fwd_gemm(g, s);

@@ -172,10 +172,12 @@ def test_split_full_size_precision(api, orc):
     _check_terms(orc, ctx, x, h, w.nu, w.k_lo, w.k_hi, w.eps, w.snrl_db)
 
 
-@pytest.mark.parametrize("shape", [("16x4", "1", "1"), ("32x2", "2", "1"), ("16x4", "2", "2"), ("32x2", "1", "4")])
+@pytest.mark.parametrize("shape", [("16x4x2", "1", "1"), ("32x2x2", "2", "1"), ("16x4x2", "2", "2"),
+                                   ("32x2x2", "1", "4"), ("32x4x2", "2", "1"), ("16x8x4", "2", "1")])
 def test_split_pipeline_variants(api, orc, shape, monkeypatch):
     """Other pipeline shapes of the tensor-core kernel (samples per stage x
-    stages, pairs per CTA, CTAs per multicast cluster) give the same chi."""
+    B stages x A stages, pairs per CTA, CTAs per multicast cluster) give the
+    same chi and loss."""
     cfg, tiles, cluster = shape
     monkeypatch.setenv("SQNGD_GEMM_CFG", cfg)
     monkeypatch.setenv("SQNGD_GEMM_TILES", tiles)
