@@ -50,7 +50,11 @@ class AfState(ctypes.Structure):
     ]
 
 
-# name -> (restype, argtypes); every symbol include/sqngd.h declares
+class WsConfig(ctypes.Structure):
+    _fields_ = [("M", c_int32), ("N", c_int32), ("B", c_int32), ("cond", c_double * 5)]
+
+
+# name -> (restype, argtypes); every symbol include/sqngd.h and include/warmstart.h declare
 SIGNATURES = {
     "af_init": (c_int32, [ctypes.POINTER(AfConfig), c_void_p, ctypes.POINTER(c_void_p)]),
     "af_destroy": (c_int32, [c_void_p]),
@@ -70,6 +74,17 @@ SIGNATURES = {
     "af_eval_hard": (c_int32, [c_void_p, c_void_p, c_void_p, P_double]),
     "af_loss_terms_noalloc": (c_int32, [c_int32, c_int32, c_int32, c_double, c_int32, c_int32, c_double, c_double,
                                         c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ws_param_count": (c_int64, []),
+    "ws_create": (c_int32, [c_int32, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
+    "ws_destroy": (c_int32, [c_void_p]),
+    "ws_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ws_set_params": (c_int32, [c_void_p, P_float]),
+    "ws_get_params": (c_int32, [c_void_p, P_float]),
+    "ws_forward": (c_int32, [c_void_p, ctypes.POINTER(WsConfig), c_int32, c_void_p, c_void_p, c_void_p]),
+    "ws_loss_grad": (c_int32, [c_void_p, ctypes.POINTER(WsConfig), c_int32, c_void_p, c_void_p, P_double,
+                               P_float]),
+    "ws_train_step": (c_int32, [c_void_p, ctypes.POINTER(WsConfig), c_int32, c_void_p, c_void_p, c_float,
+                                P_double]),
 }
 
 _lock = threading.Lock()

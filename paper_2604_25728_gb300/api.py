@@ -220,3 +220,97 @@ class AfLoss(torch.autograd.Function):
         gu, gh = fctx.saved_tensors
         s = g.to(torch.float32)
         return gu * s, gh * s, None
+
+
+# ------------------------------------------------------------ warm start --
+def ws_cond(M: int, N: int, B: int, window: float, kmax: int):
+    """The five conditioning scalars of the warm-start network for a problem
+    of M waveforms of N chips, B levels, Doppler half-width `window`
+    (cycles/chip) and delay half-width `kmax`."""
+    return [M / 8.0, N / 1024.0, B / 64.0, 10.0 * float(window), float(kmax) / N]
+
+
+class WarmStart:
+    """One ws_net: the warm-start network's FP16/FP32 parameters, Adam state
+    and activations for up to batch_max designs of up to n_max chips."""
+
+    def __init__(self, batch_max: int, n_max: int, device=None, stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.batch_max, self.n_max = int(batch_max), int(n_max)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            handle = ctypes.c_void_p()
+            st = self.lib.ws_create(self.batch_max, self.n_max, ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(handle))
+            self._check(st, None)
+        self.handle = handle
+
+    @staticmethod
+    def param_count() -> int:
+        return int(_lib.load().ws_param_count())
+
+    def _check(self, st, handle):
+        if st != _lib.AF_OK:
+            msg = self.lib.ws_last_error(handle).decode() if handle is not None else ""
+            raise AfError(st, msg)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.ws_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.param_count():
+            raise ValueError(f"expected {self.param_count()} parameters, got {p.size}")
+        self._check(self.lib.ws_set_params(self.handle, p.ctypes.data_as(_lib.P_float)), self.handle)
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.param_count(), dtype=np.float32)
+        self._check(self.lib.ws_get_params(self.handle, p.ctypes.data_as(_lib.P_float)), self.handle)
+        return p
+
+    @staticmethod
+    def _cfg(M, N, B, cond):
+        c = _lib.WsConfig(M=int(M), N=int(N), B=int(B))
+        for i in range(5):
+            c.cond[i] = float(cond[i])
+        return c
+
+    def forward(self, b0, B, cond, logits=True):
+        """b0: int32 [batch, M, N] on the device.  Returns (logits [batch, 64, N]
+        or None, b [batch, M, N] int32)."""
+        batch, M, N = b0.shape
+        _need(b0, torch.int32, (batch, M, N), "b0")
+        cfg = self._cfg(M, N, B, cond)
+        lg = torch.empty((batch, 64, N), dtype=torch.float32, device=b0.device) if logits else None
+        b = torch.empty((batch, M, N), dtype=torch.int32, device=b0.device)
+        self._check(self.lib.ws_forward(self.handle, ctypes.byref(cfg), int(batch), _ptr(b0), _ptr(lg), _ptr(b)),
+                    self.handle)
+        return lg, b
+
+    def loss_grad(self, b0, target, B, cond):
+        batch, M, N = b0.shape
+        _need(target, torch.int32, (batch, M, N), "target")
+        cfg = self._cfg(M, N, B, cond)
+        loss = ctypes.c_double()
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        self._check(self.lib.ws_loss_grad(self.handle, ctypes.byref(cfg), int(batch), _ptr(b0), _ptr(target),
+                                          ctypes.byref(loss), g.ctypes.data_as(_lib.P_float)), self.handle)
+        return loss.value, g
+
+    def train_step(self, b0, target, B, cond, lr: float, sync: bool = True):
+        batch, M, N = b0.shape
+        _need(target, torch.int32, (batch, M, N), "target")
+        cfg = self._cfg(M, N, B, cond)
+        loss = ctypes.c_double()
+        self._check(self.lib.ws_train_step(self.handle, ctypes.byref(cfg), int(batch), _ptr(b0), _ptr(target),
+                                           float(lr), ctypes.byref(loss) if sync else None), self.handle)
+        return loss.value if sync else None

@@ -1,7 +1,7 @@
 """C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
-every entry point include/sqngd.h declares, its ctypes structs match the C
-layout, and host-side validation rejects bad configurations before any CUDA
-call."""
+every entry point include/sqngd.h and include/warmstart.h declare, its ctypes
+structs match the C layout, and host-side validation rejects bad
+configurations before any CUDA call."""
 import ctypes
 import os
 import re
@@ -11,12 +11,14 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "sqngd.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("sqngd.h", "warmstart.h")]
 
 
 def _declared():
-    text = open(HEADER).read()
-    return sorted(set(re.findall(r"^AF_API\s+[\w\s\*]+?\b(\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    for h in HEADERS:
+        names |= set(re.findall(r"^AF_API\s+[\w\s\*]+?\b(\w+)\s*\(", open(h).read(), flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +31,8 @@ def test_header_declares_the_boundary():
     names = _declared()
     for n in ("af_init", "af_destroy", "af_loss_grad", "af_loss_grad_xh", "af_ambiguity", "quantize",
               "soft_quantize", "af_project", "sqngd_init", "sqngd_step", "af_eval_hard", "af_sync",
-              "af_last_error", "af_set_thresholds", "af_path_of"):
+              "af_last_error", "af_set_thresholds", "af_path_of", "ws_create", "ws_destroy", "ws_forward",
+              "ws_loss_grad", "ws_train_step", "ws_set_params", "ws_get_params", "ws_param_count"):
         assert n in names
 
 
@@ -51,7 +54,11 @@ def test_ctypes_structs_match_c_layout(tmp_path):
     src = tmp_path / "layout.c"
     fields_c = [f for f, _ in _lib.AfConfig._fields_]
     fields_s = [f for f, _ in _lib.AfState._fields_]
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sqngd.h"', 'int main(void){']
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sqngd.h"', '#include "warmstart.h"',
+             'int main(void){']
+    lines.append('printf("ws_config %zu\\n", sizeof(ws_config));')
+    for f, _ in _lib.WsConfig._fields_:
+        lines.append(f'printf("ws_config.{f} %zu\\n", offsetof(ws_config, {f}));')
     lines.append('printf("af_config %zu\\n", sizeof(af_config));')
     lines.append('printf("af_state %zu\\n", sizeof(af_state));')
     for f in fields_c:
@@ -63,6 +70,9 @@ def test_ctypes_structs_match_c_layout(tmp_path):
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    assert int(got["ws_config"]) == ctypes.sizeof(_lib.WsConfig)
+    for f, _ in _lib.WsConfig._fields_:
+        assert int(got[f"ws_config.{f}"]) == getattr(_lib.WsConfig, f).offset, f
     assert int(got["af_config"]) == ctypes.sizeof(_lib.AfConfig)
     assert int(got["af_state"]) == ctypes.sizeof(_lib.AfState)
     for f in fields_c:
@@ -104,3 +114,13 @@ def test_null_arguments_are_rejected(lib):
     assert lib.af_loss_grad(None, None, None, 0, None, None, None) == _lib.AF_ERR_INVALID_ARG
     assert lib.sqngd_step(None, None, 1, None) == _lib.AF_ERR_INVALID_ARG
     assert lib.af_path_of(None) == -1
+
+
+def test_warmstart_parameter_count_and_host_validation(lib):
+    from oracle import warmstart_oracle as wo
+    assert lib.ws_param_count() == wo.flatten(wo.init_params(0)).size
+    h = ctypes.c_void_p()
+    for bad in [(0, 16), (4, 0), (1 << 12, 1 << 12)]:
+        assert lib.ws_create(bad[0], bad[1], None, ctypes.byref(h)) == 1      # AF_ERR_INVALID_ARG
+        assert not h.value
+    assert lib.ws_destroy(None) == 1
