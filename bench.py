@@ -43,6 +43,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-time-to-target", action="store_true",
+                   help="skip the time-to-PSL-target experiment (run on rank 0 of a 1-GPU run by default)")
     p.add_argument("--fwd-path", default="fft", choices=["fft", "split"],
                    help="with --fwd-only: fft = the mid workload on the FFT path, split = the narrow-window "
                         "workload on the tensor-core path")
@@ -399,6 +401,16 @@ def run_ours(args):
     best = st.best.cpu().numpy()
     acc = ctx.af_eval_hard(st.u, st.h)
     tensor = _tensor_path(api, wl, dev, stream) if rank == 0 else None
+    ttt = None
+    if rank == 0 and ws == 1 and not args.no_time_to_target:
+        from paper_2604_25728_gb300 import warmstart
+        try:
+            params, rec = warmstart.load()
+        except OSError:
+            params, rec = None, None
+        ttt = warmstart.time_to_target(params)
+        ttt["warmstart_training"] = None if rec is None else {
+            k: rec[k] for k in ("designs", "outer_iterations", "epochs", "held_out_index_agreement")}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -419,6 +431,7 @@ def run_ours(args):
                          "traffic": traffic, "kernel_source_hash": khash},
             "cpu_baseline": cpu,
             "tensor_path": tensor,
+            "time_to_target": ttt,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per sqngd_step call: counters, best-record copy in, hard waveform,
             # the graph (forward + finish per evaluation), best-record copy out

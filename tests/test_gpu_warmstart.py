@@ -142,3 +142,30 @@ def test_bad_configurations_are_rejected(api):
     with pytest.raises(api.AfError, match="AF_ERR_INVALID_ARG"):
         net.forward(b0, 17, [0.0] * 5)                      # B > 16
     net.close()
+
+
+def test_pipeline_generates_trains_and_proposes(api):
+    """The training pipeline end to end at toy sizes: converged designs from
+    the optimiser, a few epochs, proposals of the right shape and range."""
+    from paper_2604_25728_gb300 import warmstart as ws
+    from paper_2604_25728_gb300 import workloads as wl
+    data = []
+    ctx = ws._ctx(2, 128, 16, 0.1, 32, 20, api.AF_PATH_SPLIT_BF16)
+    for i in range(4):
+        b0 = wl.phase_indices(500 + i, 2, 128, 16)
+        bs = ws.converge(ctx, b0, 10)
+        assert bs.shape == (2, 128) and bs.min() >= 0 and bs.max() < 16
+        data.append((2, 128, b0, bs))
+    ctx.close()
+    net, hist = ws.train(data, epochs=3, batch=4)
+    assert len(hist) == 3 and all(np.isfinite(hist)) and hist[-1] < hist[0]
+    bp = ws.propose(net, data[0][2], 16, 0.1, 20)
+    assert bp.shape == (2, 128) and bp.min() >= 0 and bp.max() < 16
+    net.close()
+
+
+def test_saved_parameters_load(api):
+    from paper_2604_25728_gb300 import warmstart as ws
+    params, rec = ws.load()
+    assert params.size == api.WarmStart.param_count() and np.all(np.isfinite(params))
+    assert rec["designs"] >= 256 and rec["held_out_index_agreement"] > 0.5
