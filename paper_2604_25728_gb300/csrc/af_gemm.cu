@@ -32,7 +32,6 @@
 namespace af {
 
 constexpr int kTM = kGemmRows;             // 128 delays per tile
-constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -41,16 +40,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 // Wait for phase `parity` of `bar`.  Gives up when another role has
-// aborted (unless `drain`) or after kTimeoutNs, which aborts the CTA.  The
+// aborted (unless `drain`) or after `limit_ns`, which aborts the CTA.  The
 // abort flag and the clock are looked at every 64 polls only.
 __device__ __noinline__ bool gwait_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                        bool drain) {
+                                        bool drain, unsigned long long limit_ns) {
     const unsigned long long t0 = gtimer();
     for (;;) {
         for (int k = 0; k < 64; ++k)
             if (tc::mbar_try_wait(bar, parity)) return true;
         if (!drain && *abort_flag) return false;
-        if (gtimer() - t0 > kTimeoutNs) {
+        if (gtimer() - t0 > limit_ns) {
             *abort_flag = 1;
             if (err) atomicOr(err, 2);
             return false;
@@ -58,9 +57,9 @@ __device__ __noinline__ bool gwait_slow(uint64_t* bar, uint32_t parity, volatile
     }
 }
 __device__ __forceinline__ bool gwait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                      bool drain) {
+                                      bool drain, unsigned long long limit_ns) {
     if (tc::mbar_try_wait(bar, parity)) return true;
-    return gwait_slow(bar, parity, abort_flag, err, drain);
+    return gwait_slow(bar, parity, abort_flag, err, drain, limit_ns);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
@@ -136,7 +135,7 @@ fwd_gemm_kernel(const GemmArgs g) {
     const int XH = 2 * kSPC * g.n_kc + kTM;                               // per tile: xs, then hs
     float2* xh_base = reinterpret_cast<float2*>(smem_raw + kSB * STAGE_BYTES);
 
-    __shared__ __align__(8) uint64_t bfull[kSB], bempty[kSB], afull[kSA], aempty[kSA], accfull;
+    __shared__ __align__(8) uint64_t bfull[kSB], bempty[kSB], afull[kSA], aempty[kSA], accfull, never;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ float rk[T][4];
@@ -178,6 +177,7 @@ fwd_gemm_kernel(const GemmArgs g) {
             tc::mbar_init(&aempty[s], 1);
         }
         tc::mbar_init(&accfull, 1);
+        tc::mbar_init(&never, 1);          // nothing arrives here (failure-detection test)
         s_abort = 0;
         tc::mbar_fence_init();
     }
@@ -222,16 +222,16 @@ fwd_gemm_kernel(const GemmArgs g) {
             for (int i = kSB; i < nch; ++i) {
                 const int s = i % kSB;
                 // every CTA of the cluster has finished with stage s
-                if (!gwait(&bempty[s], ((i / kSB) - 1) & 1, abort_flag, g.err, false)) break;
+                if (!gwait(&bempty[s], ((i / kSB) - 1) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
                 issue(i, s);
                 issued = i + 1;
             }
             // every stage this CTA expects has landed, and every MMA commit
             // the cluster sends to this CTA has arrived, before it exits
             for (int i = max(0, issued - kSB); i < issued; ++i)
-                gwait(&bfull[i % kSB], (i / kSB) & 1, abort_flag, g.err, true);
+                gwait(&bfull[i % kSB], (i / kSB) & 1, abort_flag, g.err, true, g.timeout_ns);
             for (int i = max(0, nch - kSB); i < nch; ++i)
-                gwait(&bempty[i % kSB], (i / kSB) & 1, abort_flag, g.err, true);
+                gwait(&bempty[i % kSB], (i / kSB) & 1, abort_flag, g.err, true, g.timeout_ns);
         }
     } else if (warp == WMMA) {
         // ------------------------------------------------- MMA issuer --
@@ -243,11 +243,15 @@ fwd_gemm_kernel(const GemmArgs g) {
             // constant offsets in the start-address field (address >> 4,
             // bits 0-13), so the issue loop is a few adds per MMA.
             const uint64_t dbase = tc::smem_desc(tc::smem_u32(bst), 128, (kKC / 8) * 128);
+            // failure-detection test: wait on a barrier nothing completes; the
+            // bounded wait gives up, aborts the CTA and reports a timeout
+            bool go = true;
+            if (g.test_stall) go = gwait(&never, 0, abort_flag, g.err, false, g.timeout_ns);
             constexpr uint64_t kStageStep = STAGE_BYTES >> 4, kLoStep = (NC * kKC * 2) >> 4, kKStep = 256 >> 4;
-            for (int i = 0; i < nch; ++i) {
+            for (int i = 0; go && i < nch; ++i) {
                 const int s = i % kSB, sa = i % kSA;
-                if (!gwait(&bfull[s], (i / kSB) & 1, abort_flag, g.err, false)) break;
-                if (!gwait(&afull[sa], (i / kSA) & 1, abort_flag, g.err, false)) break;
+                if (!gwait(&bfull[s], (i / kSB) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
+                if (!gwait(&afull[sa], (i / kSA) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
                 tc::fence_after_sync();
                 const uint64_t dh = dbase + (uint64_t)s * kStageStep;
                 const uint64_t dl = dh + kLoStep;
@@ -268,7 +272,7 @@ fwd_gemm_kernel(const GemmArgs g) {
                 tc::mma_commit(&aempty[sa]);
             }
             tc::mma_commit(&accfull);
-            gwait(&accfull, 0, abort_flag, g.err, true);
+            gwait(&accfull, 0, abort_flag, g.err, true, g.timeout_ns);
         }
     } else {
         // ------------------------------------ producers and epilogue --
@@ -345,7 +349,7 @@ fwd_gemm_kernel(const GemmArgs g) {
                 // one lane polls; the warp takes its verdict before the
                 // aligned tensor-memory stores
                 bool w = true;
-                if (lane == 0) w = gwait(&aempty[s], ((i / kSA) - 1) & 1, abort_flag, g.err, false);
+                if (lane == 0) w = gwait(&aempty[s], ((i / kSA) - 1) & 1, abort_flag, g.err, false, g.timeout_ns);
                 if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
                 tc::fence_after_sync();
             }
@@ -376,7 +380,7 @@ fwd_gemm_kernel(const GemmArgs g) {
         long long best_idx = 0x7fffffffffffffffLL;
         float2 best_c = make_float2(0.f, 0.f);
         bool acc_ready = ok;
-        if (lane == 0 && ok) acc_ready = gwait(&accfull, 0, abort_flag, g.err, false);
+        if (lane == 0 && ok) acc_ready = gwait(&accfull, 0, abort_flag, g.err, false, g.timeout_ns);
         if (__shfl_sync(0xffffffffu, acc_ready, 0)) {
             tc::fence_after_sync();
             const int d = d0 + r;
@@ -570,7 +574,8 @@ cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles) {
 }
 
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s) {
-    if (g.f.n_chunks * kTM < g.f.D || g.spc <= 0 || g.n_kc * g.spc < g.f.N) return cudaErrorInvalidValue;
+    if (g.f.n_chunks * kTM < g.f.D || g.spc <= 0 || g.n_kc * g.spc < g.f.N || g.timeout_ns == 0)
+        return cudaErrorInvalidValue;
     const int P = g.f.M * g.f.M;
     if (!(g.tiles == 1 || g.tiles == 2) || P % g.tiles != 0) return cudaErrorInvalidValue;
     if (!(g.csize == 1 || g.csize == 2 || g.csize == 4) || (P / g.tiles) % g.csize != 0) return cudaErrorInvalidValue;

@@ -110,6 +110,8 @@ struct GemmArgs {
     int sb, sa;                 // stages of B images (shared memory) and of lag products (tensor memory)
     int tiles;                  // pairs (delay tiles) per CTA sharing each B stage (1, or 2 when M*M is even)
     int csize;                  // CTAs per cluster sharing each B stage (1, 2 or 4; divides M*M / tiles)
+    unsigned long long timeout_ns;  // limit of every pipeline wait
+    int test_stall;             // failure-detection test: the MMA issuer waits on a barrier nothing completes
 };
 int gemm_bins_per_tile(int L);
 int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles);

@@ -121,6 +121,8 @@ struct af_ctx {
     int gemm_spc = 32, gemm_sb = 2, gemm_sa = 2;   // samples per stage, B stages, A stages
     int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
     int gemm_csize = 1;                   // CTAs per cluster sharing each B stage
+    unsigned long long gemm_timeout_ns = 2000000000ull;   // limit of every pipeline wait
+    int gemm_test_stall = 0;              // failure-detection test hook (SQNGD_GEMM_TEST_STALL)
     double2* pre64 = nullptr;
     double2* tw64 = nullptr;
     double2* E64 = nullptr;
@@ -345,6 +347,10 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
             const int v = atoi(e);
             if ((v == 1 || v == 2 || v == 4) && (P / c->gemm_tiles) % v == 0) c->gemm_csize = v;
         }
+        // failure-detection test: every forward's MMA issuer waits on a barrier
+        // that nothing completes, with a 50 ms limit
+        if (const char* e = getenv("SQNGD_GEMM_TEST_STALL"))
+            if (atoi(e) != 0) { c->gemm_test_stall = 1; c->gemm_timeout_ns = 50000000ull; }
         if (!gemm_shape_supported(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)) {
             c->err = "AF_PATH_SPLIT_BF16: pipeline shape does not fit this N and L";
             return fail(AF_ERR_UNIMPLEMENTED);
@@ -585,6 +591,8 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
         g.sa = c->gemm_sa;
         g.tiles = c->gemm_tiles;
         g.csize = c->gemm_csize;
+        g.timeout_ns = c->gemm_timeout_ns;
+        g.test_stall = c->gemm_test_stall;
         return launch_fwd_gemm(g, s);
     }
     return (c->path == AF_PATH_FFT) ? launch_fwd_fft_f32(a, s) : launch_fwd_dft_f32(a, s);

@@ -189,3 +189,25 @@ def test_split_pipeline_variants(api, orc, shape, monkeypatch):
     ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
     assert np.max(np.abs(chi - ref)) <= CHI_TOL * np.max(np.abs(ref))
     _check_terms(orc, ctx, x, h, nu, k_lo, k_hi, 0.2, 1.0)
+
+
+def test_pipeline_wait_timeout_is_reported_and_device_stays_usable(api, orc, monkeypatch):
+    """Failure detection without a fault: with the test hook the MMA issuer
+    waits on a barrier that nothing completes; the bounded wait (50 ms) gives
+    up, the CTA drains and exits, af_sync reports AF_ERR_TIMEOUT, and the
+    next context on the same device computes correct results."""
+    M, N, nu, k_lo, k_hi = 1, 64, wl.window_grid(0.1, 16), -10, 10
+    x, h = _pair(orc, 900, M, N)
+    monkeypatch.setenv("SQNGD_GEMM_TEST_STALL", "1")
+    bad = _ctx(api, M, N, 4, nu, k_lo, k_hi)
+    bad.af_forward(_dev(x), _dev(h))
+    with pytest.raises(api.AfError, match="AF_ERR_TIMEOUT"):
+        bad.af_sync()
+    bad.af_sync()                    # the flag is cleared once reported
+    bad.close()
+    monkeypatch.delenv("SQNGD_GEMM_TEST_STALL")
+    good = _ctx(api, M, N, 4, nu, k_lo, k_hi)
+    chi = good.af_ambiguity(_dev(x), _dev(h)).cpu().numpy()
+    ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
+    assert np.max(np.abs(chi - ref)) <= CHI_TOL * np.max(np.abs(ref))
+    good.af_sync()
