@@ -191,8 +191,9 @@ def _source_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic_record(kernel_hash: str):
-    path = os.path.join(PROFILES, "fwd_fft_mid_traffic.json")
+def _traffic_record(kernel_hash: str, name: str = "fwd_fft_mid_traffic.json"):
+    """DRAM bytes per launch from one ncu capture, if it was taken on these kernel sources."""
+    path = os.path.join(PROFILES, name)
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -492,7 +493,9 @@ def _tensor_path(api, wl, dev, stream):
                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                        "frac": (achieved / peak) if peak else None,
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS), of measured",
-                       "algorithmic_flops_per_launch": flops, "kernel_source_hash": khash}
+                       "algorithmic_flops_per_launch": flops,
+                       "traffic": _traffic_record(khash, "fwd_gemm_precision_traffic.json"),
+                       "kernel_source_hash": khash}
     out["speedup_fwd_vs_fp32_dft"] = out["fp32_dft"]["fwd_launch_us"] / out["split_bf16"]["fwd_launch_us"]
     return out
 
