@@ -82,10 +82,39 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     if (a.ctr_inc != nullptr && blockIdx.x == 0 && tid == 0) a.ctr_inc[0] += 1;
 
     const C zero = mk((T)0, (T)0);
-    for (int n = tid; n < XS; n += kThreads) xs[n] = (n < N) ? cmul(a.x[(size_t)m * N + n], a.pre[n]) : zero;
-    for (int i = tid; i < 2 * N + XS; i += kThreads) {
-        const int p = i - N;
-        hp[i] = (p >= 0 && p < N) ? a.h[(size_t)l * N + p] : zero;
+    // operand fill: every load of a batch is in flight before the first store
+    {
+        constexpr int FB = 4;
+        const C* xm = a.x + (size_t)m * N;
+        const C* hl = a.h + (size_t)l * N;
+        for (int n0 = tid; n0 < XS; n0 += kThreads * FB) {
+            C xv[FB], pv[FB];
+#pragma unroll
+            for (int q = 0; q < FB; ++q) {
+                const int n = n0 + q * kThreads;
+                xv[q] = (n < N) ? xm[n] : zero;
+                pv[q] = (n < N) ? a.pre[n] : zero;
+            }
+#pragma unroll
+            for (int q = 0; q < FB; ++q) {
+                const int n = n0 + q * kThreads;
+                if (n < XS) xs[n] = cmul(xv[q], pv[q]);
+            }
+        }
+        for (int i0 = tid; i0 < 2 * N + XS; i0 += kThreads * FB) {
+            C hv[FB];
+#pragma unroll
+            for (int q = 0; q < FB; ++q) {
+                const int i = i0 + q * kThreads;
+                const int p = i - N;
+                hv[q] = (p >= 0 && p < N && i < 2 * N + XS) ? hl[p] : zero;
+            }
+#pragma unroll
+            for (int q = 0; q < FB; ++q) {
+                const int i = i0 + q * kThreads;
+                if (i < 2 * N + XS) hp[i] = hv[q];
+            }
+        }
     }
 
     // chi_mm(0, 0) = h_m^H x_m in FP64 (Eq. 38), once per waveform.

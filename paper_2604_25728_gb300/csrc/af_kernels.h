@@ -46,9 +46,6 @@ struct FwdArgs {
     int pdl;               // launch with programmatic stream serialisation
 };
 
-// Strips (CTAs) per waveform row of the finish kernel.
-int fin_strips(int N);
-
 // Dense adjoint of the p-norm sidelobe loss on the FFT grid (same launch
 // geometry as the forward pass).
 struct AdjArgs {

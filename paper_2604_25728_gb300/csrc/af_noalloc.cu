@@ -182,6 +182,7 @@ extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, doub
         f.pkey = pkey; f.pidx = pidx; f.pchi = pchi; f.cdiag = cdiag;
         f.weight_mode = WM_UNIFORM; f.w0 = (float)(1.0 / N);
         f.eps = eps; f.ptar = pow(10.0, -snrl_db / 20.0); f.inv_N = 1.0 / N;
+        f.snrl_coef = (1.0 - eps) * (2.0 / M) / N;
         f.grid_fft = 1; f.pre = pre; f.wL = wL;
         f.x = (const float2*)x_dev; f.h_in = (const float2*)h_dev;
         f.mode = FIN_GRAD_XH; f.terms = terms_dev;

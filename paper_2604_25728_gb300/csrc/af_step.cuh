@@ -38,6 +38,7 @@ struct FinArgs {
     float w0;
     const float* wmap;        // [D][L]
     double eps, ptar;
+    double snrl_coef;         // (1 - eps) (2 / M) / N: G_m = snrl_coef (p_m - p_tar) c_m / |c_m|
     double inv_N;             // 1/N
     int pdl;                  // launch with programmatic stream serialisation
     float half_p;             // p/2 (0 = exact max)
@@ -82,10 +83,6 @@ struct FinArgs {
     float2* best_h;
     double snrl_db;
     double p_accept2;         // (10^{-(snrl_db + 0.05)/20})^2: a design is acceptable when min p_m^2 >= this
-    // projection across the CTAs of one row (FIN_ADAM_H): partial ||h||^2 per
-    // strip, and a per-row arrival counter (zero between launches)
-    double* norm_part;        // [M][strips]
-    unsigned int* row_ctr;    // [M]
 };
 
 struct AccArgs {

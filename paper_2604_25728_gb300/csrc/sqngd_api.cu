@@ -145,8 +145,6 @@ struct af_ctx {
     float2* pchi = nullptr;    // [nblk] chi at each forward CTA's best cell
     float2* adj_part = nullptr;    // [nblk][2][N] dense-adjoint partial rows (p-norm loss)
     float2* dense = nullptr;       // [2][M][N] summed dense sidelobe gradient
-    double* norm_part = nullptr;   // [M][strips] partial filter energies
-    unsigned int* row_ctr = nullptr;  // [M] arrival counters of the finish kernel
     double* pkey64 = nullptr;
     long long* pidx64 = nullptr;
     double2* cdiag = nullptr;
@@ -223,7 +221,7 @@ static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
                     c->xs, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
-                    c->ctr, c->best2, c->log, c->pchi, c->norm_part, c->row_ctr, c->adj_part, c->dense,
+                    c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->dense,
                     c->bimg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -495,8 +493,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     const size_t MN = (size_t)M * N;
     if ((s = dalloc(c, &c->pkey, c->nblk)) || (s = dalloc(c, &c->pidx, c->nblk)) ||
         (s = dalloc(c, &c->pvmax, c->nblk)) || (s = dalloc(c, &c->psum, c->nblk)) ||
-        (s = dalloc(c, &c->pchi, c->nblk)) || (s = dalloc(c, &c->norm_part, (size_t)M * fin_strips(N))) ||
-        (s = dalloc(c, &c->row_ctr, M)) ||
+        (s = dalloc(c, &c->pchi, c->nblk)) ||
         (s = dalloc(c, &c->pkey64, c->acc_nblk)) || (s = dalloc(c, &c->pidx64, c->acc_nblk)) ||
         (s = dalloc(c, &c->cdiag, M)) || (s = dalloc(c, &c->xs, MN)) || (s = dalloc(c, &c->dydz, MN)) ||
         (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
@@ -506,8 +503,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     if (cfg->pnorm > 0.0 &&
         ((s = dalloc(c, &c->adj_part, (size_t)c->nblk * 2 * N)) || (s = dalloc(c, &c->dense, 2 * MN))))
         return fail(s);
-    if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->row_ctr, 0, sizeof(unsigned int) * M) != cudaSuccess) {
+    if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) {
         c->err = "cudaMemset failed";
         return fail(AF_ERR_CUDA);
     }
@@ -624,7 +620,6 @@ static FinArgs fin_args(af_ctx* c) {
     f.M = c->cfg.M; f.N = c->cfg.N; f.L = c->cfg.L; f.D = c->D; f.k_lo = c->cfg.k_lo;
     f.nblk = c->nblk; f.ctas_per_pair = c->ctas_per_pair;
     f.pkey = c->pkey; f.pidx = c->pidx; f.pvmax = c->pvmax; f.psum = c->psum; f.pchi = c->pchi;
-    f.norm_part = c->norm_part; f.row_ctr = c->row_ctr;
     f.cdiag = c->cdiag;
     f.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM;
     f.w0 = c->w0; f.wmap = c->wmap;
@@ -632,6 +627,7 @@ static FinArgs fin_args(af_ctx* c) {
     f.inv_N = 1.0 / c->cfg.N;
     f.pdl = c->pdl ? 1 : 0;
     f.ptar = pow(10.0, -c->cfg.snrl_db / 20.0);
+    f.snrl_coef = (1.0 - c->cfg.eps) * (2.0 / c->cfg.M) / c->cfg.N;
     f.half_p = (float)(c->cfg.pnorm * 0.5);
     f.grid_fft = c->grid_fft ? 1 : 0;
     f.pre = c->pre; f.wL = c->wL; f.E = c->E;
