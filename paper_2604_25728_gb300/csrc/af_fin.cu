@@ -195,12 +195,19 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         }
         if (m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = p;
     } else if (warp == 1 && opt) {
-        if (lane == 0) { s_ctr[0] = cv0; s_ctr[1] = cv1; s_ctr[2] = cv2; s_ctr[3] = cv3; }
+        if (lane == 0) {
+            s_ctr[0] = cv0; s_ctr[1] = cv1; s_ctr[2] = cv2; s_ctr[3] = cv3;
+            // Adam step counter and bias corrections 1 - beta^t = -expm1(t ln beta), FP32
+            const long long o = cv0 - 1;
+            const long long t = (MODE == FIN_ADAM_H) ? cv1 + o * a.n_h + a.inner + 1 : cv2 + o * a.n_x + a.inner + 1;
+            s_adam[0] = -expm1f((float)t * log1pf(a.b1 - 1.f));
+            s_adam[1] = -expm1f((float)t * log1pf(a.b2 - 1.f));
+        }
         if (lane < 8) s_best[lane] = bv;
     }
     __syncthreads();
 
-    // ---- 3. class values, loss, winning cell, Adam constants -------------------
+    // ---- 3. class values, loss, winning cell, best-design record --------------
     if (tid == 0) {
         double cvv[2];
         long long cell[2];
@@ -264,11 +271,6 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (!isfinite(s_terms[0]) && a.err_flag) atomicOr(a.err_flag, 1);
         }
         if (opt) {
-            // Adam step counter and bias corrections 1 - beta^t = -expm1(t ln beta), FP32
-            const long long t = (MODE == FIN_ADAM_H) ? s_ctr[1] + o * a.n_h + a.inner + 1
-                                                       : s_ctr[2] + o * a.n_x + a.inner + 1;
-            s_adam[0] = -expm1f((float)t * log1pf(a.b1 - 1.f));
-            s_adam[1] = -expm1f((float)t * log1pf(a.b2 - 1.f));
             s_ok = 0;
             if (MODE == FIN_ADAM_H && a.snap_best) {
                 // best-design record: this evaluation scored the hard design (X_hard, H)
