@@ -351,14 +351,13 @@ def run_ours(args):
     for _ in range(10):
         ctx.af_forward(xh, st.h)
     torch.cuda.synchronize()
-    fwd_ms = []
+    # average launch duration: R back-to-back launches between two events
+    fe0.record(stream)
     for _ in range(R):
-        fe0.record(stream)
         ctx.af_forward(xh, st.h)
-        fe1.record(stream)
-        fe1.synchronize()
-        fwd_ms.append(fe0.elapsed_time(fe1))
-    fwd_s = float(np.mean(fwd_ms)) / 1e3
+    fe1.record(stream)
+    fe1.synchronize()
+    fwd_s = fe0.elapsed_time(fe1) / R / 1e3
     flops = _fwd_flops(w)
     peak, peak_note = _fp32_peak_tflops()
     achieved = flops / fwd_s / 1e12
@@ -429,6 +428,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "fwd_fft_kernel<512> (af_forward)", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_note,
                          "algorithmic_flops_per_launch": flops, "launch_us": fwd_s * 1e6,
+                         "launch_timing": f"{R} back-to-back af_forward launches between two CUDA events",
                          "traffic": traffic, "kernel_source_hash": khash},
             "cpu_baseline": cpu,
             "tensor_path": tensor,
@@ -464,17 +464,16 @@ def _tensor_path(api, wl, dev, stream):
     e1 = torch.cuda.Event(enable_timing=True)
 
     def timed(fn, reps):
+        """Average duration over `reps` back-to-back calls between two events."""
         for _ in range(5):
             fn()
         torch.cuda.synchronize()
-        ms = []
+        e0.record(stream)
         for _ in range(reps):
-            e0.record(stream)
             fn()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return float(np.mean(ms)) / 1e3
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
 
     out = {"workload": w.name}
     for name, path, reps in (("split_bf16", api.AF_PATH_SPLIT_BF16, 200), ("fp32_dft", api.AF_PATH_DFT, 40)):

@@ -245,6 +245,7 @@ cudaError_t adj_prepare(int L, int N, int E) {
     return adj_any(a, nullptr, true);
 }
 int adj_smem_bytes(int L, int N, int E) {
+    if (E != 8 && E != 16) return -1;   // the adjoint is built for 8 and 16 values per thread
     const bool e8 = (E == 8);
     switch (L) {
         case 32: return e8 ? adj_smem<32, 8>(N) : adj_smem<32, 16>(N);

@@ -43,20 +43,34 @@ __device__ __forceinline__ constexpr double w16s(int s) {
          : s == 6 ? 0.70710678118654752440 : 0.38268343236508977173;
 }
 
-// Multiply o by e^{+j 2 pi s / R} (s < R/2, R <= 16), folding the trivial cases.
+// e^{+j 2 pi s / 32} for s = 1, 3, 5, ..., 15 (odd multiples of pi/16).
+__device__ __forceinline__ constexpr double w32c(int s) {
+    return s == 1 ? 0.980785280403230449126 : s == 3 ? 0.831469612302545237079 : s == 5 ? 0.555570233019602224743
+         : s == 7 ? 0.195090322016128267848 : s == 9 ? -0.195090322016128267848
+         : s == 11 ? -0.555570233019602224743 : s == 13 ? -0.831469612302545237079 : -0.980785280403230449126;
+}
+__device__ __forceinline__ constexpr double w32s(int s) {
+    return s == 1 ? 0.195090322016128267848 : s == 3 ? 0.555570233019602224743 : s == 5 ? 0.831469612302545237079
+         : s == 7 ? 0.980785280403230449126 : s == 9 ? 0.980785280403230449126
+         : s == 11 ? 0.831469612302545237079 : s == 13 ? 0.555570233019602224743 : 0.195090322016128267848;
+}
+
+// Multiply o by e^{+j 2 pi s / R} (s < R/2, R <= 32), folding the trivial cases.
 template <int R, int S, typename C>
 __device__ __forceinline__ C twiddle_const(C o) {
     using T = decltype(o.x);
-    constexpr int s16 = S * (16 / R);
-    if constexpr (s16 == 0) return o;
-    else if constexpr (s16 == 4) return cmulj(o);
-    else if constexpr (s16 == 2 || s16 == 6) {
+    constexpr int s32 = S * (32 / R);
+    if constexpr (s32 == 0) return o;
+    else if constexpr (s32 == 8) return cmulj(o);
+    else if constexpr (s32 == 4 || s32 == 12) {
         constexpr T r2 = (T)0.70710678118654752440;
         // e^{j pi/4} = r2 (1 + j); e^{j 3pi/4} = r2 (-1 + j)
-        if constexpr (s16 == 2) return mk((o.x - o.y) * r2, (o.x + o.y) * r2);
+        if constexpr (s32 == 4) return mk((o.x - o.y) * r2, (o.x + o.y) * r2);
         else return mk((-o.x - o.y) * r2, (o.x - o.y) * r2);
+    } else if constexpr ((s32 & 1) == 0) {
+        return cmul(o, mk((T)w16c(s32 / 2), (T)w16s(s32 / 2)));
     } else {
-        return cmul(o, mk((T)w16c(s16), (T)w16s(s16)));
+        return cmul(o, mk((T)w32c(s32), (T)w32s(s32)));
     }
 }
 
@@ -97,7 +111,7 @@ template <int ST> struct Dft<1, ST> {
 constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
 template <int L, int E> struct Plan {
-    static_assert(E == 8 || E == 16, "E must be 8 or 16");
+    static_assert(E == 8 || E == 16 || E == 32, "E must be 8, 16 or 32");
     static_assert(L >= 2 * E && L <= 4096 && (L & (L - 1)) == 0, "L must be a power of two in [2E, 4096]");
     static constexpr int T = L / E;
     static constexpr int lgE = ilog2c(E);

@@ -318,6 +318,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     for (int j = 0; uniform && j < L; ++j)
         if (fabs(c->nu[j] - (c->nu0 + (double)j / L)) > 1e-12) uniform = false;
     c->fft_e = uniform ? fft_default_elems(L, false) : 0;
+    // the dense adjoint of the p-norm loss shares the forward's twiddle
+    // tables and is built for 8 and 16 values per thread
+    if (cfg->pnorm > 0.0 && c->fft_e == 32) c->fft_e = 16;
     const int fft_smem = uniform ? fft_smem_bytes(L, N, false, c->fft_e) : -1;
     uniform = uniform && fft_smem > 0 && fft_smem <= 227 * 1024;
     if (cfg->path == AF_PATH_FFT && !uniform) {

@@ -59,10 +59,11 @@ FFT_CASES = [
 ]
 
 
-@pytest.mark.parametrize("elems", ["8", "16"])
+@pytest.mark.parametrize("elems", ["8", "16", "32"])
 @pytest.mark.parametrize("case", FFT_CASES)
 def test_ambiguity_fft_matches_oracle(api, orc, case, elems, monkeypatch):
-    """Both register-FFT shapes (8 or 16 values per thread) against the oracle."""
+    """Every register-FFT shape (8, 16 or 32 values per thread; a shape that
+    does not fit the row length falls back to the default) against the oracle."""
     monkeypatch.setenv("SQNGD_FFT_E", elems)
     M, N, L, k_lo, k_hi, nu0 = case
     nu = nu0 + np.arange(L) / L
