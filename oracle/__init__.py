@@ -252,6 +252,59 @@ def sqngd_outer(state, cfg):
     return losses, wpsl
 
 
+# ---------------------------------------------------------------- SQNAF (h = x)
+def grad_matched(x, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, pnorm=0.0, use_cell=None):
+    """Loss L(x, x) and its total gradient when every filter is its waveform
+    (SQNAF, Section IV); returns (terms, g)."""
+    x = _c128(x)
+    M, N = x.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    terms = np.zeros(6)
+    g = np.zeros_like(x)
+    uc = None if use_cell is None else (ctypes.c_longlong * 1)(int(use_cell))
+    lib().or_grad_matched(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                          ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(x), uc, _d(terms), _d(g))
+    return terms, g
+
+
+def loss_grad_u_matched(u, rho, a, c, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5,
+                        pnorm=0.0, use_cell=None):
+    """SQNAF loss of the soft waveform and its gradient w.r.t. the logits."""
+    u = _f64(u)
+    M, N = u.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    terms = np.zeros(6)
+    gu = np.zeros((M, N))
+    uc = None if use_cell is None else (ctypes.c_longlong * 1)(int(use_cell))
+    lib().or_loss_grad_u_matched(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                                 ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(u),
+                                 rho.size, _d(_f64(rho)), ctypes.c_double(a), ctypes.c_double(c),
+                                 uc, _d(terms), _d(gu))
+    return terms, gu
+
+
+def sqnaf_outer(state, cfg):
+    """One outer iteration of SQNAF (Step A skipped, the hard design scored
+    first); state holds float64 u, mu, vu and t_x, updated in place.
+    Returns the 1 + n_x losses and L_WPSL values."""
+    M, N = state["u"].shape
+    nu, w = _grid(cfg["nu"], cfg["k_lo"], cfg["k_hi"], cfg.get("weights"))
+    rho = _f64(cfg["rho"])
+    n_ev = 1 + cfg["n_x"]
+    losses = np.zeros(n_ev)
+    wpsl = np.zeros(n_ev)
+    tx = ctypes.c_longlong(state["t_x"])
+    lib().or_sqnaf_outer(
+        M, N, nu.size, _d(nu), cfg["k_lo"], cfg["k_hi"], _d(w), ctypes.c_double(cfg["eps"]),
+        ctypes.c_double(cfg["snrl_db"]), ctypes.c_double(cfg.get("pnorm", 0.0)),
+        cfg["B"], rho.size, _d(rho), ctypes.c_double(cfg["a"]), ctypes.c_double(cfg["c"]),
+        cfg["n_x"], ctypes.c_double(cfg["lr_x"]), ctypes.c_double(cfg.get("b1", 0.9)),
+        ctypes.c_double(cfg.get("b2", 0.999)), ctypes.c_double(cfg.get("adam_eps", 1e-8)),
+        _d(state["u"]), _d(state["mu"]), _d(state["vu"]), ctypes.byref(tx), _d(losses), _d(wpsl))
+    state["t_x"] = tx.value
+    return losses, wpsl
+
+
 def metrics(x, h, nu, k_lo, k_hi, weights=None):
     """(APSL dB, CPSL dB, PSLR dB, max SNRL dB) and per-waveform SNRL (Eqs. 10, 48)."""
     x, h = _c128(x), _c128(h)

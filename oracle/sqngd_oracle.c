@@ -576,6 +576,81 @@ void or_sqngd_outer(int M, int N, int L, const double* nu, int k_lo, int k_hi,
 }
 
 /* ------------------------------------------------------------------------ */
+/* SQNAF (Section IV): the delay-Doppler WPSL objective with no receive-     */
+/* filter optimisation -- every filter is the waveform itself, h = x, so     */
+/* the loss is L(x, x) and, by the chain rule through both arguments,        */
+/*   grad L(x, x) = grad_x L(x, h) + grad_h L(x, h)   at h = x.              */
+/* Same real-pair convention and use_cell meaning as or_grad_xh.             */
+/* ------------------------------------------------------------------------ */
+void or_grad_matched(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                     const double* w, double eps, double snrl_db, double pnorm,
+                     const double* x_ri, const long long* use_cell,
+                     double* terms, double* g_ri)
+{
+    int n = M * N;
+    double* gh = (double*)malloc(sizeof(double) * 2 * n);
+    or_grad_xh(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, x_ri, x_ri, use_cell,
+               terms, g_ri, gh);
+    for (int e = 0; e < 2 * n; ++e) g_ri[e] += gh[e];
+    free(gh);
+}
+
+/* The transmit chain of Section III-A on the SQNAF loss: x = soft(u), the
+ * gradient of L(x, x) mapped to the logits as in or_loss_grad_u. */
+void or_loss_grad_u_matched(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                            const double* w, double eps, double snrl_db, double pnorm,
+                            const double* u, int K, const double* rho, double a, double c,
+                            const long long* use_cell, double* terms, double* gu)
+{
+    int n = M * N;
+    double* x = (double*)malloc(sizeof(double) * 2 * n);
+    double* dy = (double*)malloc(sizeof(double) * n);
+    double* g = (double*)malloc(sizeof(double) * 2 * n);
+    or_soft_waveform(M, N, u, K, rho, a, c, x, dy);
+    or_grad_matched(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, x, use_cell, terms, g);
+    const cplx* xc = (const cplx*)x;
+    const cplx* gc = (const cplx*)g;
+    for (int e = 0; e < n; ++e) {
+        double gy = TWO_PI * cimag(conj(xc[e]) * gc[e]);
+        double z = 1.0 / (1.0 + exp(-u[e]));
+        gu[e] = gy * dy[e] * z * (1.0 - z);
+    }
+    free(x); free(dy); free(g);
+}
+
+/* One outer iteration of SQNAF: Step (A) of Algorithm 1 is skipped (there
+ * is no filter to update); the hard design is scored once, L(X_hard,
+ * X_hard), then N_x x {X_soft from u; grad_u L(X_soft, X_soft); Adam on u}.
+ * losses_out / wpsl_out receive 1 + N_x values: the score first. */
+void or_sqnaf_outer(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                    const double* w, double eps, double snrl_db, double pnorm,
+                    int B, int K, const double* rho, double a, double c,
+                    int n_x, double lr_x, double b1, double b2, double adam_eps,
+                    double* u, double* mu, double* vu, long long* t_x,
+                    double* losses_out, double* wpsl_out)
+{
+    int n = M * N;
+    double* xh = (double*)malloc(sizeof(double) * 2 * n);
+    double* gu = (double*)malloc(sizeof(double) * n);
+    double* pm = (double*)malloc(sizeof(double) * M);
+    double terms[6];
+    long long cells[2];
+    or_hard_waveform(M, N, u, K, rho, B, NULL, xh);
+    or_loss(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, xh, xh, terms, pm, cells);
+    if (losses_out) losses_out[0] = terms[0];
+    if (wpsl_out) wpsl_out[0] = terms[1];
+    for (int j = 0; j < n_x; ++j) {
+        or_loss_grad_u_matched(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, u, K, rho, a, c,
+                               NULL, terms, gu);
+        if (losses_out) losses_out[1 + j] = terms[0];
+        if (wpsl_out) wpsl_out[1 + j] = terms[1];
+        *t_x += 1;
+        or_adam(n, u, gu, mu, vu, *t_x, lr_x, b1, b2, adam_eps);
+    }
+    free(xh); free(gu); free(pm);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Acceptance metrics: PSLR (Eq. 48) of the auto and cross terms over the    */
 /* ROI (cells of positive weight; auto excludes tau = 0 as in Eq. 8) and the */
 /* SNRL of Eq. 10 for every m.                                               */

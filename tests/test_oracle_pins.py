@@ -404,3 +404,96 @@ def test_grad_at_cell_equals_full_gradient_at_that_cell(orc):
         np.testing.assert_allclose(gh2, gh, atol=1e-14)
         full = orc.ambiguity(x, h, nu, -(N - 1), N - 1).reshape(-1)
         assert abs(chi - full[cell]) < 1e-12
+
+
+# ------------------------------------------------------------------ SQNAF (h = x)
+def test_matched_gradient_matches_finite_differences(orc):
+    """SQNAF takes every filter equal to its waveform: the gradient of
+    L(x, x) against central differences of the loss with both arguments
+    moved together.  Non-unimodular x so that the SNRL term also contributes;
+    a one-sided delay window and an offset grid so the max is unique."""
+    M, N = 2, 10
+    x = wl.unit_phasors(21, M, N) + 0.4 * wl.complex_normal(21, M, N)
+    nu = 0.0137 + np.arange(8) / 8
+    k_lo, k_hi = 1, 6
+    for eps in (0.1, 0.7):
+        _, g = orc.grad_matched(x, nu, k_lo, k_hi, eps=eps, snrl_db=0.5)
+        idx = (wl.uniform(22, 16, 3) * (M * N)).astype(int)
+        for t, i in enumerate(idx):
+            m, n = divmod(int(i), N)
+            e = 1.0 if t % 2 == 0 else 1j
+            def f(s):
+                xx = x.copy()
+                xx[m, n] += s * e
+                return orc.loss(xx, xx, nu, k_lo, k_hi, eps=eps, snrl_db=0.5)["loss"]
+            fd = (f(1e-6) - f(-1e-6)) / 2e-6
+            an = g[m, n].real if e == 1.0 else g[m, n].imag
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (eps, m, n, fd, an)
+
+
+def test_matched_gradient_is_sum_of_partials_and_not_either_alone(orc):
+    """The matched gradient is neither partial alone: with h = x both the
+    transmit and the filter side move."""
+    M, N = 2, 12
+    x = wl.unit_phasors(23, M, N)
+    nu = 0.021 + np.arange(8) / 8
+    _, g = orc.grad_matched(x, nu, 1, 9, eps=0.3)
+    _, gx, gh = orc.grad_xh(x, x, nu, 1, 9, eps=0.3)
+    np.testing.assert_allclose(g, gx + gh, atol=1e-15)
+    assert np.max(np.abs(gh)) > 0.1 * np.max(np.abs(g)) and np.max(np.abs(gx)) > 0.1 * np.max(np.abs(g))
+
+
+def test_matched_snrl_term_has_no_phase_gradient(orc):
+    """With h = x a unimodular waveform has p_m = 1 whatever its phases, so
+    the SNRL term (eps = 0) is constant along the transmit chain: dL/du = 0."""
+    M, N, B, r_n = 2, 16, 4, 3
+    rho, a = orc.thresholds(B, r_n)
+    u = wl.logits(24, M, N, scale=1.5)
+    t, gu = orc.loss_grad_u_matched(u, rho, a, 40.0, wl.full_grid(16), -(N - 1), N - 1, eps=0.0,
+                                    snrl_db=1.0)
+    ptar = 10 ** (-1.0 / 20)
+    assert abs(t[4] - (1 - ptar) ** 2) < 1e-12
+    assert np.max(np.abs(gu)) < 1e-12
+
+
+def test_matched_soft_chain_matches_finite_differences(orc):
+    M, N, B, r_n = 2, 12, 4, 3
+    rho, a = orc.thresholds(B, r_n)
+    c = 40.0
+    u = wl.logits(25, M, N, scale=1.5)
+    kw = dict(nu=0.011 + np.arange(8) / 8, k_lo=1, k_hi=8, eps=0.3, snrl_db=0.5)
+    _, gu = orc.loss_grad_u_matched(u, rho, a, c, **kw)
+    for i in (wl.uniform(25, 12, 5) * M * N).astype(int):
+        m, n = divmod(int(i), N)
+        up, um = u.copy(), u.copy()
+        up[m, n] += 1e-6
+        um[m, n] -= 1e-6
+        fd = (orc.loss_grad_u_matched(up, rho, a, c, **kw)[0][0]
+              - orc.loss_grad_u_matched(um, rho, a, c, **kw)[0][0]) / 2e-6
+        assert abs(fd - gu[m, n]) <= 1e-5 * max(1.0, abs(gu[m, n])), (m, n, fd, gu[m, n])
+    # the loss is that of the soft waveform used as its own filter
+    xs, _ = orc.soft_waveform(u, rho, a, c)
+    r = orc.loss(xs, xs, **kw)
+    assert abs(orc.loss_grad_u_matched(u, rho, a, c, **kw)[0][0] - r["loss"]) < 1e-14
+
+
+def test_sqnaf_outer_iteration_structure(orc):
+    """SQNAF outer iteration: the first value scores (X_hard, X_hard); one
+    transmit step is Adam on u with the matched soft-chain gradient."""
+    w = wl.small(2, 16, 4, 16, r_n=5)
+    rho, a = orc.thresholds(w.B, w.r_n)
+    b = wl.phase_indices(2, w.M, w.N, w.B)
+    u = orc.init_logits(b, w.B, w.r_n)
+    st = dict(u=u.copy(), mu=np.zeros_like(u), vu=np.zeros_like(u), t_x=0)
+    cfg = dict(nu=w.nu, k_lo=w.k_lo, k_hi=w.k_hi, eps=w.eps, snrl_db=w.snrl_db, B=w.B,
+               rho=rho, a=a, c=w.c, n_x=1, lr_x=1e-2)
+    losses, wpsl = orc.sqnaf_outer(st, cfg)
+    x0 = np.exp(2j * np.pi * b / w.B)
+    r0 = orc.loss(x0, x0, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db)
+    assert abs(losses[0] - r0["loss"]) < 1e-14 and abs(wpsl[0] - r0["wpsl"]) < 1e-14
+    t1, gu = orc.loss_grad_u_matched(u, rho, a, w.c, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db)
+    assert abs(losses[1] - t1[0]) < 1e-14
+    theta, m, v = u.copy(), np.zeros_like(u), np.zeros_like(u)
+    orc.adam(theta, gu, m, v, 1, 1e-2)
+    np.testing.assert_array_equal(st["u"], theta)
+    assert st["t_x"] == 1
