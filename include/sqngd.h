@@ -99,6 +99,10 @@ typedef struct af_config {
     int32_t n_h, n_x;        /* inner Adam steps on H and on the transmit logits (Alg. 1) */
     double lr_h, lr_x;       /* Adam learning rates (eta_h, eta_x) */
     double beta1, beta2, adam_eps;  /* Adam constants; 0 selects 0.9, 0.999, 1e-8 */
+    int32_t matched;         /* 0: joint design (SQNGD).  1: SQNAF (Section IV): every
+                                receive filter is its waveform, h_m = x_m, so there is no
+                                filter to optimise (needs n_h = 0); losses and gradients
+                                are those of L(x, x) and filter arguments are ignored */
 } af_config;
 
 /*
@@ -173,6 +177,9 @@ AF_API af_status af_forward(af_ctx* ctx, const float* x_dev, const float* h_dev)
  * The exact max is differentiated at one cell per class: the largest
  * w^2|chi|^2 in FP32, ties to the lowest linear cell index; WAPSL wins a tie
  * with WCPSL.
+ * Matched contexts (cfg.matched = 1): h_dev is ignored (may be NULL), the
+ * loss is L(x, x), grad_x_dev receives its total gradient (the sum of the
+ * transmit and filter partials at h = x) and grad_h_dev must be NULL.
  */
 AF_API af_status af_loss_grad_xh(af_ctx* ctx, const float* x_dev, const float* h_dev,
                           double* terms_dev, float* grad_x_dev, float* grad_h_dev);
@@ -184,6 +191,8 @@ AF_API af_status af_loss_grad_xh(af_ctx* ctx, const float* x_dev, const float* h
  * use_hard = 1.  u_dev: [M][N]; h_dev complex [M][N];
  * grad_u_dev: [M][N] (ignored when use_hard = 1), grad_h_dev complex [M][N];
  * terms_dev as in af_loss_grad_xh.  Any output may be NULL.
+ * Matched contexts: h_dev is ignored (may be NULL), grad_u_dev is the
+ * gradient of L(x, x) and grad_h_dev must be NULL.
  */
 AF_API af_status af_loss_grad(af_ctx* ctx, const float* u_dev, const float* h_dev, int32_t use_hard,
                        double* terms_dev, float* grad_u_dev, float* grad_h_dev);
@@ -227,6 +236,11 @@ AF_API af_status sqngd_init(af_ctx* ctx, const int32_t* b_dev, const float* nois
  * log_host: if not NULL, receives [n_outer][n_h + n_x][4] doubles (L, L_WPSL,
  * L_SNRL, winning class) and the call synchronises; otherwise it is
  * asynchronous.  Advances st->t_h, st->t_x, st->outer.
+ * Matched contexts (SQNAF): Step A is skipped and h_dev, m_h_dev, v_h_dev are
+ * not touched (they may be NULL); each outer iteration scores the hard design
+ * L(X_hard, X_hard) for the best-design record, then runs the n_x transmit
+ * steps on L(X_soft, X_soft); best_h receives X_hard of the best design and
+ * the log has 1 + n_x evaluations per outer iteration (the score first).
  */
 AF_API af_status sqngd_step(af_ctx* ctx, af_state* st, int32_t n_outer, double* log_host);
 
@@ -236,6 +250,8 @@ AF_API af_status sqngd_step(af_ctx* ctx, af_state* st, int32_t n_outer, double* 
  * [2] PSLR dB = max of the two, [3] max_m SNRL dB, then SNRL dB for each m.
  * PSL is max |chi| over the ROI (cells of positive weight; the auto term
  * skips tau = 0).  out_host: [4 + M] doubles.  Synchronous.
+ * Matched contexts: h_dev is ignored (may be NULL); the filters are the hard
+ * waveforms.
  */
 AF_API af_status af_eval_hard(af_ctx* ctx, const float* u_dev, const float* h_dev, double* out_host);
 

@@ -36,6 +36,7 @@ class AfConfig(ctypes.Structure):
         ("n_h", c_int32), ("n_x", c_int32),
         ("lr_h", c_double), ("lr_x", c_double),
         ("beta1", c_double), ("beta2", c_double), ("adam_eps", c_double),
+        ("matched", c_int32),
     ]
 
 

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 import torch
@@ -36,7 +37,7 @@ class Context:
 
     def __init__(self, M, N, B, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, r_n=100,
                  c=300.0, pnorm=0.0, path=AF_PATH_AUTO, n_h=10, n_x=10, lr_h=5e-2, lr_x=5e-4,
-                 beta1=0.9, beta2=0.999, adam_eps=1e-8, device=None, stream=None):
+                 beta1=0.9, beta2=0.999, adam_eps=1e-8, matched=False, device=None, stream=None):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.M, self.N, self.B = int(M), int(N), int(B)
@@ -47,6 +48,7 @@ class Context:
         self.r_n, self.c = int(r_n), float(c)
         self.K = self.B * self.r_n
         self.n_h, self.n_x = int(n_h), int(n_x)
+        self.matched = bool(matched)
         w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
         if w is not None and w.shape != (self.D, self.L):
             raise ValueError(f"weights must be [D, L] = [{self.D}, {self.L}]")
@@ -56,7 +58,7 @@ class Context:
             weights=None if w is None else w.ctypes.data_as(_lib.P_float),
             eps=float(eps), snrl_db=float(snrl_db), r_n=self.r_n, c=self.c, pnorm=float(pnorm),
             path=int(path), n_h=self.n_h, n_x=self.n_x, lr_h=float(lr_h), lr_x=float(lr_x),
-            beta1=float(beta1), beta2=float(beta2), adam_eps=float(adam_eps))
+            beta1=float(beta1), beta2=float(beta2), adam_eps=float(adam_eps), matched=int(self.matched))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream()
             handle = ctypes.c_void_p()
@@ -112,14 +114,20 @@ class Context:
         self._mn(x, "x", True); self._mn(h, "h", True)
         self._check(self.lib.af_forward(self.handle, _ptr(x), _ptr(h)))
 
+    def _filters(self, h):
+        """Filters argument: ignored by matched (SQNAF) contexts, which may pass None."""
+        if h is None and self.matched:
+            return None
+        return self._mn(h, "h", True)
+
     def af_loss_grad_xh(self, x, h, terms=None, grad_x=None, grad_h=None):
-        self._mn(x, "x", True); self._mn(h, "h", True)
+        self._mn(x, "x", True); h = self._filters(h)
         terms = self.empty_terms() if terms is None else terms
         self._check(self.lib.af_loss_grad_xh(self.handle, _ptr(x), _ptr(h), _ptr(terms), _ptr(grad_x), _ptr(grad_h)))
         return terms, grad_x, grad_h
 
     def af_loss_grad(self, u, h, use_hard=False, terms=None, grad_u=None, grad_h=None):
-        self._mn(u, "u"); self._mn(h, "h", True)
+        self._mn(u, "u"); h = self._filters(h)
         terms = self.empty_terms() if terms is None else terms
         self._check(self.lib.af_loss_grad(self.handle, _ptr(u), _ptr(h), int(bool(use_hard)), _ptr(terms),
                                           _ptr(grad_u), _ptr(grad_h)))
@@ -156,14 +164,15 @@ class Context:
         cs = state.c_struct()
         buf = None
         if log:
-            buf = np.zeros((n_outer, self.n_h + self.n_x, 4), dtype=np.float64)
+            evals = (1 + self.n_x) if self.matched else (self.n_h + self.n_x)
+            buf = np.zeros((n_outer, evals, 4), dtype=np.float64)
         self._check(self.lib.sqngd_step(self.handle, ctypes.byref(cs), int(n_outer),
                                         None if buf is None else buf.ctypes.data_as(_lib.P_double)))
         state.t_h, state.t_x, state.outer = cs.t_h, cs.t_x, cs.outer
         return buf
 
     def af_eval_hard(self, u, h):
-        self._mn(u, "u"); self._mn(h, "h", True)
+        self._mn(u, "u"); h = self._filters(h)
         out = np.zeros(4 + self.M, dtype=np.float64)
         self._check(self.lib.af_eval_hard(self.handle, _ptr(u), _ptr(h), out.ctypes.data_as(_lib.P_double)))
         return out
@@ -173,11 +182,11 @@ class Context:
 class SqngdState:
     """Device buffers of the optimiser state (caller-owned, see af_state)."""
     u: torch.Tensor
-    h: torch.Tensor
+    h: Optional[torch.Tensor]
     m_u: torch.Tensor
     v_u: torch.Tensor
-    m_h: torch.Tensor
-    v_h: torch.Tensor
+    m_h: Optional[torch.Tensor]
+    v_h: Optional[torch.Tensor]
     best_q: torch.Tensor
     best_h: torch.Tensor
     best: torch.Tensor
@@ -186,19 +195,22 @@ class SqngdState:
     outer: int = 0
 
     @classmethod
-    def create(cls, u, h):
+    def create(cls, u, h=None):
+        """h = None: matched (SQNAF) state, no filters and no filter moments."""
         z = torch.zeros_like
         best = torch.tensor([float("inf"), float("inf"), -1.0, float("inf")], dtype=torch.float64,
                             device=u.device)
-        return cls(u=u, h=h, m_u=z(u), v_u=z(u), m_h=z(h), v_h=z(h),
-                   best_q=torch.zeros(u.shape, dtype=torch.int32, device=u.device), best_h=h.clone(),
+        best_h = torch.zeros(u.shape, dtype=torch.complex64, device=u.device) if h is None else h.clone()
+        return cls(u=u, h=h, m_u=z(u), v_u=z(u), m_h=None if h is None else z(h), v_h=None if h is None else z(h),
+                   best_q=torch.zeros(u.shape, dtype=torch.int32, device=u.device), best_h=best_h,
                    best=best)
 
     def c_struct(self):
-        return _lib.AfState(u_dev=self.u.data_ptr(), h_dev=self.h.data_ptr(), m_u_dev=self.m_u.data_ptr(),
-                            v_u_dev=self.v_u.data_ptr(), m_h_dev=self.m_h.data_ptr(), v_h_dev=self.v_h.data_ptr(),
-                            best_q_dev=self.best_q.data_ptr(), best_h_dev=self.best_h.data_ptr(),
-                            best_dev=self.best.data_ptr(), t_h=self.t_h, t_x=self.t_x, outer=self.outer)
+        p = lambda t: 0 if t is None else t.data_ptr()
+        return _lib.AfState(u_dev=p(self.u), h_dev=p(self.h), m_u_dev=p(self.m_u),
+                            v_u_dev=p(self.v_u), m_h_dev=p(self.m_h), v_h_dev=p(self.v_h),
+                            best_q_dev=p(self.best_q), best_h_dev=p(self.best_h),
+                            best_dev=p(self.best), t_h=self.t_h, t_x=self.t_x, outer=self.outer)
 
 
 class AfLoss(torch.autograd.Function):

@@ -12,9 +12,10 @@
 //     grad h_l*(p) += conj(g) x_m*(p-k*) e^{+j 2 pi nu* (p-k*)},  g = eps w chi*/|chi*|
 // plus the SNRL term at (m, m, 0, 0) and, in the p-norm variant, the dense
 // partial gradients of the adjoint kernel.  The chain to the logits is
-// dL/du = 2 pi Im(conj(x) grad x) Q_A'(z) z(1-z).  In the optimiser modes the
-// CTA applies Adam to its strip; for the filters the projection of Eq. 32
-// needs the row's norm: every strip puts its FP64 partial in shared memory,
+// dL/du = 2 pi Im(conj(x) grad x) Q_A'(z) z(1-z).  With matched filters
+// (SQNAF, h = x) the waveform takes both partial gradients, grad x + grad h.
+// In the optimiser modes the CTA applies Adam to its strip; for the filters
+// the projection of Eq. 32 needs the row's norm: every strip puts its FP64 partial in shared memory,
 // the cluster synchronises, and every CTA sums the partials of its cluster in
 // rank order through distributed shared memory (same sum everywhere, no
 // global round trip).  A CTA reads other rows only in the gradient gather,
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             xm[i] = a.x[e];
             hm[i] = a.h_in[e];
             if (MODE == FIN_ADAM_H) { mh[i] = a.m_h[e]; vh[i] = a.v_h[e]; if (a.snap_best) uu[i] = a.u[e]; }
+            if (MODE == FIN_SCORE && a.snap_best) uu[i] = a.u[e];
             if (MODE == FIN_ADAM_U) { uu[i] = a.u[e]; mu[i] = a.m_u[e]; vu[i] = a.v_u[e]; dy[i] = a.dydz[e]; }
             if (MODE == FIN_GRAD_U && a.grad_u != nullptr) { uu[i] = a.u[e]; dy[i] = a.dydz[e]; }
         }
@@ -116,12 +118,13 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     // ---- 1. one batch of loads of everything the previous kernels wrote -------
     double2 cm = make_double2(0.0, 0.0);
     if (warp == 0 && lane < M) cm = a.cdiag[lane];
-    const bool opt = (MODE == FIN_ADAM_H || MODE == FIN_ADAM_U) && a.ctr != nullptr;
+    constexpr bool kSnap = (MODE == FIN_ADAM_H || MODE == FIN_SCORE);   // may take the best-design record
+    const bool opt = (MODE == FIN_ADAM_H || MODE == FIN_ADAM_U || MODE == FIN_SCORE) && a.ctr != nullptr;
     long long cv0 = 0, cv1 = 0, cv2 = 0, cv3 = 0;
     double bv = 0.0;
     if (warp == 1 && opt) {
         if (lane == 0) { cv0 = a.ctr[0]; cv1 = a.ctr[1]; cv2 = a.ctr[2]; cv3 = a.ctr[3]; }
-        if (MODE == FIN_ADAM_H && a.snap_best && lane < 8) bv = a.best2[lane];
+        if (kSnap && a.snap_best && lane < 8) bv = a.best2[lane];
     }
     float kb[2] = {-1.f, -1.f};
     long long ib[2] = {0x7fffffffffffffffLL, 0x7fffffffffffffffLL};
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         }
         if (opt) {
             s_ok = 0;
-            if (MODE == FIN_ADAM_H && a.snap_best) {
+            if (kSnap && a.snap_best) {
                 // best-design record: this evaluation scored the hard design (X_hard, H)
                 const double* prev = s_best + ((o + 1) & 1) * 4;
                 double* cur = a.best2 + (o & 1) * 4;
@@ -291,8 +294,9 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     }
     __syncthreads();
 
-    const bool need_gx = (MODE != FIN_ADAM_H);
-    const bool need_gh = (MODE != FIN_ADAM_U);
+    // matched filters (SQNAF): h = x, so x takes both partial gradients
+    const bool need_gx = (MODE != FIN_ADAM_H && MODE != FIN_SCORE);
+    const bool need_gh = (MODE != FIN_SCORE) && (MODE != FIN_ADAM_U || a.matched);
     const int ms = s_cell[0], ls_ = s_cell[1], ks = s_cell[2], js = s_cell[3];
     const float2 g = s_g, Gm = s_G;
 
@@ -329,6 +333,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                     if (need_gh) gh[i] = cadd(gh[i], base[(size_t)M * N + e]);
                 }
             }
+            if (a.matched) gx[i] = cadd(gx[i], gh[i]);
         }
     }
 
@@ -405,6 +410,18 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             a.h[(size_t)m * N + n] = hp;
             bad |= !isfinite(hp.x) || !isfinite(hp.y);
         }
+    } else if (MODE == FIN_SCORE) {
+        // the scored design is (X_hard, X_hard): record it if it is the best so far
+        if (a.snap_best && s_ok) {
+#pragma unroll
+            for (int i = 0; i < EPT; ++i) {
+                const int n = n_base + tid + i * kFT;
+                if (n >= N) continue;
+                const size_t e = (size_t)m * N + n;
+                if (a.best_h) a.best_h[e] = xm[i];
+                if (a.best_q) a.best_q[e] = hard_q(a.qa, sigmoidf_(uu[i]));
+            }
+        }
     } else {  // FIN_ADAM_U
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
@@ -474,6 +491,7 @@ cudaError_t launch_fin(const FinArgs& a, cudaStream_t s) {
         case FIN_GRAD_U: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_GRAD_U>, a);
         case FIN_ADAM_H: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_ADAM_H>, a);
         case FIN_ADAM_U: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_ADAM_U>, a);
+        case FIN_SCORE: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_SCORE>, a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -70,16 +70,22 @@ __global__ void soft_quantize_z_kernel(const float* __restrict__ z, long long n,
     if (x) x[i] = xv;
 }
 
-// FP64 hard waveform and FP64 copy of the filters for the acceptance pass.
+// FP64 hard waveform and FP64 copy of the filters for the acceptance pass
+// (h == nullptr: matched filters, h64 = x64).
 __global__ void wave_hard_f64_kernel(const float* __restrict__ u, const float2* __restrict__ h, int n,
                                      QuantArgs q, const double2* __restrict__ level64,
                                      double2* __restrict__ x64, double2* __restrict__ h64) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int qq = hard_q(q, sigmoidf_(u[i]));
-    x64[i] = level64[qq % q.B];
-    const float2 hv = h[i];
-    h64[i] = make_double2((double)hv.x, (double)hv.y);
+    const double2 xv = level64[qq % q.B];
+    x64[i] = xv;
+    if (h == nullptr) {
+        h64[i] = xv;
+    } else {
+        const float2 hv = h[i];
+        h64[i] = make_double2((double)hv.x, (double)hv.y);
+    }
 }
 
 // -------------------------------------------------------------- projection --

@@ -20,7 +20,8 @@ enum FinMode : int {
     FIN_GRAD_XH = 0,   // write grad_x, grad_h
     FIN_GRAD_U = 1,    // write grad_u (soft chain) and grad_h
     FIN_ADAM_H = 2,    // Adam on (H_Re, H_Im) + projection (Step A)
-    FIN_ADAM_U = 3     // Adam on u (Step B)
+    FIN_ADAM_U = 3,    // Adam on u (Step B)
+    FIN_SCORE = 4      // loss and best-design record only (SQNAF's score of the hard design)
 };
 
 enum NextWave : int { NEXT_NONE = 0, NEXT_SOFT = 1, NEXT_HARD = 2 };
@@ -83,6 +84,7 @@ struct FinArgs {
     float2* best_h;
     double snrl_db;
     double p_accept2;         // (10^{-(snrl_db + 0.05)/20})^2: a design is acceptable when min p_m^2 >= this
+    int matched;              // SQNAF: h = x, the gradient of x is the sum of both partials
 };
 
 struct AccArgs {

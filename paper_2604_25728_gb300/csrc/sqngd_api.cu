@@ -273,6 +273,8 @@ static af_status validate(const af_config* g, std::string* why) {
     if (g->path < AF_PATH_AUTO || g->path > AF_PATH_SPLIT_BF16) return bad("unknown path");
     if (g->n_h < 0 || g->n_x < 0 || g->n_h + g->n_x < 1 || g->n_h + g->n_x > 256)
         return bad("n_h, n_x must be >= 0 with 1 <= n_h + n_x <= 256");
+    if (g->matched != 0 && g->matched != 1) return bad("matched must be 0 or 1");
+    if (g->matched && g->n_h != 0) return bad("matched (SQNAF) has no filter step: n_h must be 0");
     for (int j = 0; j < g->L; ++j)
         if (!isfinite(g->nu[j])) return bad("nu has a non-finite value");
     if (g->weights) {
@@ -618,6 +620,12 @@ static cudaError_t launch_eval_forward(af_ctx* c, const float2* x, const float2*
     return launch_adj(d, s);
 }
 
+// Evaluations per outer iteration: Step A and Step B, or (matched) one score
+// of the hard design and Step B.
+static int evals_per_outer(const af_ctx* c) {
+    return c->cfg.matched ? 1 + c->cfg.n_x : c->cfg.n_h + c->cfg.n_x;
+}
+
 static FinArgs fin_args(af_ctx* c) {
     FinArgs f{};
     f.M = c->cfg.M; f.N = c->cfg.N; f.L = c->cfg.L; f.D = c->D; f.k_lo = c->cfg.k_lo;
@@ -642,7 +650,8 @@ static FinArgs fin_args(af_ctx* c) {
         f.p_accept2 = p * p;
     }
     f.n_h = c->cfg.n_h; f.n_x = c->cfg.n_x;
-    f.evals_per_outer = c->cfg.n_h + c->cfg.n_x;
+    f.evals_per_outer = evals_per_outer(c);
+    f.matched = c->cfg.matched;
     if (c->cfg.pnorm > 0.0) { f.dense_g = c->dense; f.n_dense = 1; }
     f.lr = 0.f;
     f.b1 = (float)c->cfg.beta1; f.b2 = (float)c->cfg.beta2; f.adam_eps = (float)c->cfg.adam_eps;
@@ -670,6 +679,10 @@ extern "C" af_status af_forward(af_ctx* c, const float* x, const float* h) {
 extern "C" af_status af_loss_grad_xh(af_ctx* c, const float* x, const float* h, double* terms, float* gx,
                                      float* gh) {
     if (!c) return AF_ERR_INVALID_ARG;
+    if (c->cfg.matched) {
+        if (gh) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_xh: matched context: grad_h must be NULL");
+        h = x;
+    }
     if (!x || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_xh: x and h must not be NULL");
     CK(c, launch_eval_forward(c, (const float2*)x, (const float2*)h, c->stream, nullptr));
     FinArgs f = fin_args(c);
@@ -686,10 +699,12 @@ extern "C" af_status af_loss_grad_xh(af_ctx* c, const float* x, const float* h, 
 extern "C" af_status af_loss_grad(af_ctx* c, const float* u, const float* h, int32_t use_hard, double* terms,
                                   float* gu, float* gh) {
     if (!c) return AF_ERR_INVALID_ARG;
-    if (!u || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad: u and h must not be NULL");
+    if (c->cfg.matched && gh) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad: matched context: grad_h must be NULL");
+    if (!u || (!h && !c->cfg.matched)) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad: u and h must not be NULL");
     const int MN = c->cfg.M * c->cfg.N;
     QuantArgs q = quant_args(c);
     float2* x = use_hard ? c->xh : c->xs;
+    if (c->cfg.matched) h = (const float*)x;
     CK(c, launch_wave_from_logits(u, MN, q, use_hard ? 1 : 0, x, c->dydz, nullptr, c->stream));
     CK(c, launch_eval_forward(c, x, (const float2*)h, c->stream, nullptr));
     FinArgs f = fin_args(c);
@@ -748,9 +763,29 @@ static bool same_state(const af_state& a, const af_state& b) {
 static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
     const int nh = c->cfg.n_h, nx = c->cfg.n_x;
     const int MN = c->cfg.M * c->cfg.N;
+    const bool matched = c->cfg.matched != 0;
     float2* h = (float2*)st->h_dev;
     bool first = true;
-    if (nh == 0) CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 0, c->xs, c->dydz, nullptr, s));
+    if (matched) {
+        // SQNAF: score the hard design with its own matched filters (best-design
+        // record), then prepare the soft waveform of the first transmit step
+        CK(c, launch_eval_forward(c, c->xh, c->xh, s, c->ctr));
+        first = false;
+        FinArgs f = fin_args(c);
+        f.mode = FIN_SCORE;
+        f.x = c->xh; f.h_in = c->xh;
+        f.u = st->u_dev;
+        f.ctr = c->ctr; f.inner = 0;
+        f.log = c->log; f.eval_index = 0;
+        f.snap_best = 1;
+        f.best2 = c->best2; f.best_q = st->best_q_dev; f.best_h = (float2*)st->best_h_dev;
+        f.next_wave = (nx > 0) ? NEXT_SOFT : NEXT_HARD;
+        f.x_next = (nx > 0) ? c->xs : c->xh;
+        f.dydz_next = c->dydz;
+        CK(c, launch_fin(f, s));
+    } else if (nh == 0) {
+        CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 0, c->xs, c->dydz, nullptr, s));
+    }
     for (int i = 0; i < nh; ++i) {
         CK(c, launch_eval_forward(c, c->xh, h, s, first ? c->ctr : nullptr));
         first = false;
@@ -769,15 +804,16 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
         CK(c, launch_fin(f, s));
     }
     for (int j = 0; j < nx; ++j) {
-        CK(c, launch_eval_forward(c, c->xs, h, s, first ? c->ctr : nullptr));
+        const float2* hx = matched ? c->xs : h;
+        CK(c, launch_eval_forward(c, c->xs, hx, s, first ? c->ctr : nullptr));
         first = false;
         FinArgs f = fin_args(c);
         f.mode = FIN_ADAM_U;
-        f.x = c->xs; f.dydz = c->dydz; f.h_in = h;
+        f.x = c->xs; f.dydz = c->dydz; f.h_in = hx;
         f.u = st->u_dev; f.m_u = st->m_u_dev; f.v_u = st->v_u_dev;
         f.lr = (float)c->cfg.lr_x;
         f.ctr = c->ctr; f.inner = j;
-        f.log = c->log; f.eval_index = nh + j;
+        f.log = c->log; f.eval_index = (matched ? 1 : nh) + j;
         f.next_wave = (j == nx - 1) ? NEXT_HARD : NEXT_SOFT;
         f.x_next = (j == nx - 1) ? c->xh : c->xs;
         f.dydz_next = c->dydz;
@@ -788,11 +824,12 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
 
 extern "C" af_status sqngd_step(af_ctx* c, af_state* st, int32_t n_outer, double* log_host) {
     if (!c) return AF_ERR_INVALID_ARG;
-    if (!st || !st->u_dev || !st->h_dev || !st->m_u_dev || !st->v_u_dev || !st->m_h_dev || !st->v_h_dev)
+    if (!st || !st->u_dev || !st->m_u_dev || !st->v_u_dev ||
+        (!c->cfg.matched && (!st->h_dev || !st->m_h_dev || !st->v_h_dev)))
         FAIL(c, AF_ERR_INVALID_ARG, "sqngd_step: state buffers must not be NULL");
     if (n_outer < 0) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_step: n_outer < 0");
     if (n_outer == 0) return AF_OK;
-    const int ev = c->cfg.n_h + c->cfg.n_x;
+    const int ev = evals_per_outer(c);
     const int MN = c->cfg.M * c->cfg.N;
 
     // log capacity (the captured graph indexes the log by the device counter)
@@ -832,7 +869,7 @@ extern "C" af_status sqngd_step(af_ctx* c, af_state* st, int32_t n_outer, double
     }
     CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 1, c->xh, nullptr, nullptr, c->cap));
     for (int o = 0; o < n_outer; ++o) CK(c, cudaGraphLaunch(c->gexec, c->cap));
-    if (st->best_dev && c->cfg.n_h > 0)
+    if (st->best_dev && (c->cfg.n_h > 0 || c->cfg.matched))
         CK(c, launch_copy_f64(st->best_dev, c->best2 + ((n_outer - 1) & 1) * 4, 4, c->cap));
     if (log_host)
         CK(c, cudaMemcpyAsync(log_host, c->log, sizeof(double) * (size_t)n_outer * ev * 4, cudaMemcpyDeviceToHost, c->cap));
@@ -848,7 +885,8 @@ extern "C" af_status sqngd_step(af_ctx* c, af_state* st, int32_t n_outer, double
 // ------------------------------------------------------------- acceptance --
 extern "C" af_status af_eval_hard(af_ctx* c, const float* u, const float* h, double* out_host) {
     if (!c) return AF_ERR_INVALID_ARG;
-    if (!u || !h || !out_host) FAIL(c, AF_ERR_INVALID_ARG, "af_eval_hard: NULL pointer");
+    if (c->cfg.matched) h = nullptr;     // the filters are the hard waveforms
+    if (!u || (!h && !c->cfg.matched) || !out_host) FAIL(c, AF_ERR_INVALID_ARG, "af_eval_hard: NULL pointer");
     const int M = c->cfg.M, N = c->cfg.N, MN = M * N;
     CK(c, launch_wave_hard_f64(u, (const float2*)h, MN, quant_args(c), c->level64, c->x64, c->h64, c->stream));
     FwdArgs<double2, double> a{};

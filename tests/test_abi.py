@@ -95,7 +95,8 @@ def _cfg(**kw):
 @pytest.mark.parametrize("bad", [dict(M=0), dict(M=17), dict(N=1), dict(N=5000), dict(B=1), dict(k_lo=-40),
                                  dict(k_lo=3, k_hi=2), dict(eps=1.5), dict(snrl_db=-1.0), dict(r_n=0),
                                  dict(c=0.0), dict(pnorm=0.5), dict(path=9), dict(n_h=0, n_x=0),
-                                 dict(L=0), dict(nu=[0.0, float("nan")])])
+                                 dict(L=0), dict(nu=[0.0, float("nan")]),
+                                 dict(matched=1, n_h=1, n_x=1), dict(matched=2, n_h=0)])
 def test_init_rejects_bad_config_on_host(lib, bad):
     from paper_2604_25728_gb300 import _lib
     cfg, nu = _cfg(**bad)

@@ -31,10 +31,10 @@ def _pair(orc, seed, M, N, noise=0.3):
     return x, h
 
 
-def _evals_per_s(api, ctx, w, seed):
+def _evals_per_s(api, ctx, w, seed, matched=False):
     b = torch.from_numpy(wl.phase_indices(seed, w.M, w.N, w.B)).cuda()
     u, h = ctx.sqngd_init(b)
-    st = api.SqngdState.create(u, h)
+    st = api.SqngdState.create(u, None if matched else h)
     ctx.sqngd_step(st, 2, log=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -44,21 +44,28 @@ def _evals_per_s(api, ctx, w, seed):
     e1.record()
     e1.synchronize()
     ctx.af_sync()
-    return n * (w.n_h + w.n_x) / (e0.elapsed_time(e1) / 1e3)
+    evals = (1 + w.n_x) if matched else (w.n_h + w.n_x)
+    return n * evals / (e0.elapsed_time(e1) / 1e3)
 
 
 ROWS = [("tiny", "auto"), ("mid", "auto"), ("precision", "dft"), ("precision", "split"),
-        ("learned", "dft"), ("learned", "split"), ("differentiation", "auto")]
+        ("learned", "dft"), ("learned", "split"), ("differentiation", "auto"), ("mid", "sqnaf")]
 
 
 @pytest.mark.parametrize("which,path", ROWS)
 def test_error_report(api, orc, which, path):
+    """path "sqnaf": the matched-filter variant (h = x, no filter step) on the
+    FFT path; its rate counts the hard-design score of each outer iteration."""
     w = getattr(wl, which)()
-    p = {"auto": api.AF_PATH_AUTO, "dft": api.AF_PATH_DFT, "split": api.AF_PATH_SPLIT_BF16}[path]
+    matched = path == "sqnaf"
+    p = {"auto": api.AF_PATH_AUTO, "sqnaf": api.AF_PATH_AUTO, "dft": api.AF_PATH_DFT,
+         "split": api.AF_PATH_SPLIT_BF16}[path]
     chi_tol, db_tol = (1e-4, 0.1) if path == "split" else (1e-5, 0.05)
     x, h = _pair(orc, 77, w.M, w.N)
+    if matched:
+        h = x
     ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
-                      n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x, path=p)
+                      n_h=0 if matched else w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x, path=p, matched=matched)
     xd, hd = torch.from_numpy(x).cuda(), torch.from_numpy(h).cuda()
     # |chi| on sampled cells (every cell of small grids)
     total = w.M * w.M * w.D * w.L
@@ -71,15 +78,20 @@ def test_error_report(api, orc, which, path):
     chi_err = np.max(np.abs(got - ref)) / w.N
     # loss terms, winning cell, gradient there
     gx = torch.empty((w.M, w.N), dtype=torch.complex64, device="cuda")
-    gh = torch.empty_like(gx)
+    gh = None if matched else torch.empty_like(gx)
     terms, _, _ = ctx.af_loss_grad_xh(xd, hd, grad_x=gx, grad_h=gh)
     ctx.af_sync()
     t = terms.cpu().numpy()
     cell = int(t[6 + int(t[5])])
     chi_c, ogx, ogh = orc.grad_at_cell(x, h, w.nu, w.k_lo, w.k_hi, cell, 1.0 / w.N, eps=w.eps,
                                        snrl_db=w.snrl_db)
-    scale = max(np.max(np.abs(ogx)), np.max(np.abs(ogh)))
-    grad_err = max(np.max(np.abs(gx.cpu().numpy() - ogx)), np.max(np.abs(gh.cpu().numpy() - ogh))) / scale
+    if matched:
+        # h = x: the waveform's gradient is the sum of both partials
+        og = ogx + ogh
+        grad_err = np.max(np.abs(gx.cpu().numpy() - og)) / np.max(np.abs(og))
+    else:
+        scale = max(np.max(np.abs(ogx)), np.max(np.abs(ogh)))
+        grad_err = max(np.max(np.abs(gx.cpu().numpy() - ogx)), np.max(np.abs(gh.cpu().numpy() - ogh))) / scale
     if which != "differentiation":
         r = orc.loss(x, h, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db)
         dpsl = max(abs(20 * np.log10(t[g] / r[k])) for g, k in ((2, "wapsl"), (3, "wcpsl")) if r[k] > 0)
@@ -87,7 +99,7 @@ def test_error_report(api, orc, which, path):
         # max over 20,000 sampled cells cannot exceed the reported max; the reported
         # max is the oracle's |chi| at the reported cell
         dpsl = abs(20 * np.log10(t[1] / (abs(chi_c) / w.N)))
-    eps_s = _evals_per_s(api, ctx, w, 5)
+    eps_s = _evals_per_s(api, ctx, w, 5, matched)
     ctx.close()
     print(f"\n| {which} | {path} | {eps_s:,.0f} | {chi_err:.1e} | {dpsl:.4f} | {grad_err:.1e} |")
     assert chi_err <= chi_tol
