@@ -45,9 +45,9 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-time-to-target", action="store_true",
                    help="skip the time-to-PSL-target experiment (run on rank 0 of a 1-GPU run by default)")
-    p.add_argument("--fwd-path", default="fft", choices=["fft", "split"],
+    p.add_argument("--fwd-path", default="fft", choices=["fft", "split", "corr"],
                    help="with --fwd-only: fft = the mid workload on the FFT path, split = the narrow-window "
-                        "workload on the tensor-core path")
+                        "workload on the tensor-core path, corr = the zero-Doppler correlation setting (L = 1)")
     p.add_argument("--fwd-only", type=int, default=0,
                    help="run only N launches of the fused forward pass on the workload (for profiler captures)")
     return p.parse_args()
@@ -175,6 +175,16 @@ def _split_flops(w) -> float:
     return 3 * 8.0 * P * valid * w.L
 
 
+def _corr_flops(w) -> float:
+    """Algorithmic FLOPs of one single-bin (cross-correlation) forward launch:
+    8 per complex multiply-add of a valid lag product (the phasor of the one
+    bin is applied once per sample) plus 3 per cell for |chi|^2."""
+    P = w.M * w.M
+    n = np.arange(w.k_lo, w.k_hi + 1)
+    valid = np.clip(w.N - np.abs(n), 0, None).sum()
+    return 8.0 * P * valid + 3.0 * P * w.D
+
+
 def _measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -283,9 +293,13 @@ def run_ours(args):
 
     w = _workload()
     seed = rank_seed(rank)
-    if args.fwd_only > 0 and args.fwd_path == "split":
-        w = wl.precision()
-        ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, path=api.AF_PATH_SPLIT_BF16)
+    if args.fwd_only > 0 and args.fwd_path in ("split", "corr"):
+        if args.fwd_path == "split":
+            w = wl.precision()
+            ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, path=api.AF_PATH_SPLIT_BF16)
+        else:
+            w = wl.correlation()
+            ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
         x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
         for _ in range(args.fwd_only):
             ctx.af_forward(x, x)
@@ -401,6 +415,7 @@ def run_ours(args):
     best = st.best.cpu().numpy()
     acc = ctx.af_eval_hard(st.u, st.h)
     tensor = _tensor_path(api, wl, dev, stream) if rank == 0 else None
+    variants = _variants(api, wl, dev, stream) if rank == 0 else None
     ttt = None
     if rank == 0 and ws == 1 and not args.no_time_to_target:
         from paper_2604_25728_gb300 import warmstart
@@ -432,6 +447,7 @@ def run_ours(args):
                          "traffic": traffic, "kernel_source_hash": khash},
             "cpu_baseline": cpu,
             "tensor_path": tensor,
+            "variants": variants,
             "time_to_target": ttt,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per sqngd_step call: counters, best-record copy in, hard waveform,
@@ -496,6 +512,63 @@ def _tensor_path(api, wl, dev, stream):
                        "traffic": _traffic_record(khash, "fwd_gemm_precision_traffic.json"),
                        "kernel_source_hash": khash}
     out["speedup_fwd_vs_fp32_dft"] = out["fp32_dft"]["fwd_launch_us"] / out["split_bf16"]["fwd_launch_us"]
+    return out
+
+
+def _variants(api, wl, dev, stream):
+    """The correlation setting (L = 1, nu = 0: the single-bin correlation
+    kernel) and the SQNAF mode (matched filters) on the mid workload: forward
+    launch time, roofline and optimiser evaluations/s through sqngd_step."""
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    def step_rate(c, w, matched, n_outer=20):
+        b = torch.from_numpy(wl.phase_indices(5, w.M, w.N, w.B)).to(dev)
+        u, h = c.sqngd_init(b)
+        st = api.SqngdState.create(u, None if matched else h)
+        c.sqngd_step(st, 2, log=False)
+        dt = timed(lambda: c.sqngd_step(st, n_outer, log=False), 1)
+        c.af_sync()
+        evals = (1 + w.n_x) if matched else (w.n_h + w.n_x)
+        return n_outer * evals / dt
+
+    out = {}
+    w = wl.correlation()
+    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                    lr_h=w.lr_h, lr_x=w.lr_x)
+    x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
+    h = x.clone()
+    fwd = timed(lambda: c.af_forward(x, h), 200)
+    flops = _corr_flops(w)
+    peak, note = _fp32_peak_tflops()
+    out["correlation"] = {
+        "workload": w.name, "kernel": "fwd_corr_kernel (af_forward, L = 1)",
+        "fwd_launch_us": fwd * 1e6, "sqngd_evals_per_s": step_rate(c, w, False),
+        "roofline": {"bound": "alu", "achieved": flops / fwd / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / fwd / 1e12 / peak, "peak_source": note,
+                     "algorithmic_flops_per_launch": flops,
+                     "launch_timing": "200 back-to-back af_forward launches between two CUDA events"}}
+    c.close()
+    w = wl.mid()
+    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                    n_h=0, n_x=w.n_x, lr_x=w.lr_x, matched=True)
+    out["sqnaf"] = {"workload": w.name + ", matched filters (h = x), no filter step",
+                    "sqngd_evals_per_s": step_rate(c, w, True),
+                    "note": "evaluations include the hard-design score of each outer iteration"}
+    c.close()
     return out
 
 

@@ -209,8 +209,148 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
     }
 }
 
+// ------------------------------------------------------------------------
+// One Doppler bin (L = 1; nu = 0 is the zero-Doppler correlation of the
+// paper's correlation experiments): chi_ml(k) = sum_n x'_m(n) conj(h_l(n+k))
+// with x' = x e^{j 2 pi nu_0 n}, a plain cross-correlation.  The tiled DFT
+// above would spend 63 of its 64 bin columns on padding, so this kernel
+// gives each CTA 32 consecutive delays of one pair (lane = delay) and splits
+// the samples n of their common range across the 8 warps.  Shared memory
+// holds x' and h over that range, relative to its first sample and
+// zero-padded, so lane t at offset i reads x'[i] (one broadcast) and
+// h[i + t] (consecutive words): no bounds checks, no bank conflicts.  The
+// warps' partial sums are added in a fixed order by warp 0, which also
+// runs the sidelobe reduction of its 32 cells.
+constexpr int kCorrThreads = 256;
+constexpr int kCorrWarps = kCorrThreads / 32;
+constexpr int TRC = 32;            // delays per CTA
+constexpr int kCorrPad = 4 * kCorrWarps + TRC;   // extra slots beyond N in each buffer
+
+template <typename C, typename K>
+__global__ void __launch_bounds__(kCorrThreads)
+fwd_corr_kernel(const FwdArgs<C, K> a) {
+    using T = decltype(C{}.x);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N;
+    C* xs = reinterpret_cast<C*>(smem_raw);      // [N + kCorrPad]
+    C* hs = xs + N + kCorrPad;                   // [N + 2 kCorrPad]
+    __shared__ C red[kCorrWarps][TRC];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_wait();
+    pdl_trigger();
+    if (a.ctr_inc != nullptr && blockIdx.x == 0 && tid == 0) a.ctr_inc[0] += 1;
+    const int pair = blockIdx.x / a.n_chunks;
+    const int chunk = blockIdx.x - pair * a.n_chunks;
+    const int m = pair / a.M, l = pair - m * a.M;
+    const int d0 = chunk * TRC;
+    const int k_first = a.k_lo + d0;
+    const int k_last = a.k_lo + min(a.D, d0 + TRC) - 1;
+    // samples with some valid product in this chunk
+    const int n_begin = max(0, -k_last);
+    const int n_end = min(N, N - k_first);
+    const int len = n_end - n_begin;                       // >= 1 for any delay in -(N-1)..N-1
+    const int S4 = 4 * ((len + 4 * kCorrWarps - 1) / (4 * kCorrWarps));   // samples per warp
+    const int span = kCorrWarps * S4;                      // < len + kCorrPad - TRC
+    const C* xg = a.x + (size_t)m * N;
+    const C* hg = a.h + (size_t)l * N;
+    for (int i = tid; i < span; i += kCorrThreads) {
+        const int n = n_begin + i;
+        xs[i] = (n < n_end) ? cmul(xg[n], a.tw[n]) : mk((T)0, (T)0);
+    }
+    const int p_lo = n_begin + k_first;
+    for (int q = tid; q < span + TRC; q += kCorrThreads) {
+        const int p = p_lo + q;
+        hs[q] = (p >= 0 && p < N) ? hg[p] : mk((T)0, (T)0);
+    }
+    if (a.cdiag != nullptr && m == l && chunk == 0) {
+        // A_mm(0, 0) in FP64 (Eq. 38)
+        double sr = 0.0, si = 0.0;
+        for (int n = tid; n < N; n += kCorrThreads) {
+            const C xv = xg[n], hv = hg[n];
+            const double xr = xv.x, xi = xv.y, hr = hv.x, hi = hv.y;
+            sr += xr * hr + xi * hi;
+            si += xi * hr - xr * hi;
+        }
+        __shared__ double rd[2][kCorrWarps];
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) { rd[0][warp] = sr; rd[1][warp] = si; }
+        __syncthreads();
+        if (tid == 0) {
+            double tr = 0.0, ti = 0.0;
+            for (int w = 0; w < kCorrWarps; ++w) { tr += rd[0][w]; ti += rd[1][w]; }
+            a.cdiag[m] = make_double2(tr, ti);
+        }
+    }
+    __syncthreads();
+
+    // lane = delay k_first + lane, warp = samples [warp S4, (warp + 1) S4) of the range
+    C acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = mk((T)0, (T)0);
+    const int i0 = warp * S4;
+    for (int i = i0; i < i0 + S4; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const C xv = xs[i + u];
+            const C hv = hs[i + u + lane];
+            acc[u].x = fma(xv.x, hv.x, acc[u].x);
+            acc[u].x = fma(xv.y, hv.y, acc[u].x);
+            acc[u].y = fma(xv.y, hv.x, acc[u].y);
+            acc[u].y = fma(-xv.x, hv.y, acc[u].y);
+        }
+    }
+    red[warp][lane] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+    __syncthreads();
+    if (warp != 0) return;
+    C v = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < kCorrWarps; ++w) v = cadd(v, red[w][lane]);
+    const int d = d0 + lane;
+    if (a.mode == FWD_DUMP) {
+        if (d < a.D) a.chi_out[(size_t)pair * a.D + d] = v;
+        return;
+    }
+    K key = (K)-1;
+    if (d < a.D && !(m == l && a.k_lo + d == 0)) {
+        key = (K)v.x * (K)v.x + (K)v.y * (K)v.y;
+        if (a.weight_mode != WM_UNIFORM) {
+            const float w = __ldg(a.wmap + d);
+            key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
+        }
+    }
+    long long idx = (key >= (K)0) ? (long long)pair * a.D + d : 0x7fffffffffffffffLL;
+    C bc = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const K ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        const T ocx = __shfl_xor_sync(0xffffffffu, bc.x, o);
+        const T ocy = __shfl_xor_sync(0xffffffffu, bc.y, o);
+        if (dbetter(ok, oi, key, idx)) { key = ok; idx = oi; bc = mk(ocx, ocy); }
+    }
+    if (lane == 0) {
+        a.pkey[blockIdx.x] = key;
+        a.pidx[blockIdx.x] = (key >= (K)0) ? idx : -1;
+        if (a.pchi) a.pchi[blockIdx.x] = bc;
+        if (a.pvmax) { a.pvmax[blockIdx.x] = 0.f; a.psum[blockIdx.x] = 0.f; }
+    }
+}
+
+template <typename C>
+static int corr_smem_bytes(int N) { return (int)sizeof(C) * (2 * N + 3 * kCorrPad); }
+
 template <typename C, typename K>
 static cudaError_t launch_dft(const FwdArgs<C, K>& a, cudaStream_t s) {
+    if (a.L == 1) {
+        const int smem = corr_smem_bytes<C>(a.N);
+        auto kern = fwd_corr_kernel<C, K>;
+        cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
+        if (e != cudaSuccess) return e;
+        return launch_ex(kern, dim3(a.M * a.M * a.n_chunks), dim3(kCorrThreads), smem, s, a.pdl != 0, a);
+    }
     const int smem = (int)sizeof(C) * (2 * a.N + NK * TR + NK * TC);
     auto kern = fwd_dft_kernel<C, K>;
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
@@ -223,13 +363,15 @@ static cudaError_t launch_dft(const FwdArgs<C, K>& a, cudaStream_t s) {
 template <typename C, typename K>
 static cudaError_t prepare_dft(int N) {
     const int smem = (int)sizeof(C) * (2 * N + NK * TR + NK * TC);
-    return set_smem_once(reinterpret_cast<const void*>(fwd_dft_kernel<C, K>), smem);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void*>(fwd_dft_kernel<C, K>), smem);
+    if (e != cudaSuccess) return e;
+    return set_smem_once(reinterpret_cast<const void*>(fwd_corr_kernel<C, K>), corr_smem_bytes<C>(N));
 }
 
 cudaError_t dft_prepare_f32(int N) { return prepare_dft<float2, float>(N); }
 cudaError_t dft_prepare_f64(int N) { return prepare_dft<double2, double>(N); }
 
-int dft_rows_per_cta() { return TR; }
+int dft_rows_per_cta(int L) { return L == 1 ? TRC : TR; }
 int dft_col_tiles(int L) { return (L + TC - 1) / TC; }
 
 cudaError_t launch_fwd_dft_f32(const FwdArgs<float2, float>& a, cudaStream_t s) { return launch_dft(a, s); }

@@ -87,8 +87,9 @@ cudaError_t fft_prepare_f64(int L, int N, int E);
 cudaError_t dft_prepare_f32(int N);
 cudaError_t dft_prepare_f64(int N);
 
-// Direct DFT path (any grid), SIMT.
-int dft_rows_per_cta();
+// Direct DFT path (any grid), SIMT; a single bin (L = 1) runs as a
+// cross-correlation kernel with its own delays per CTA.
+int dft_rows_per_cta(int L);
 int dft_col_tiles(int L);
 cudaError_t launch_fwd_dft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
 cudaError_t launch_fwd_dft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);

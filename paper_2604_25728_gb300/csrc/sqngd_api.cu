@@ -478,7 +478,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         c->n_chunks = (c->D + kGemmRows - 1) / kGemmRows;
         c->ctas_per_pair = c->n_chunks * c->gemm_n_ct;
     } else {
-        c->rows_per_chunk = dft_rows_per_cta();
+        c->rows_per_chunk = dft_rows_per_cta(L);
         c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
         c->ctas_per_pair = c->n_chunks * dft_col_tiles(L);
     }
@@ -490,7 +490,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         c->acc_n_chunks = (c->D + c->acc_rows_per_chunk - 1) / c->acc_rows_per_chunk;
         c->acc_ctas_per_pair = c->acc_n_chunks;
     } else {
-        c->acc_rows_per_chunk = dft_rows_per_cta();
+        c->acc_rows_per_chunk = dft_rows_per_cta(L);
         c->acc_n_chunks = (c->D + c->acc_rows_per_chunk - 1) / c->acc_rows_per_chunk;
         c->acc_ctas_per_pair = c->acc_n_chunks * dft_col_tiles(L);
     }

@@ -139,6 +139,14 @@ def learned() -> Workload:
                     window_grid(0.1, 128))
 
 
+def correlation() -> Workload:
+    """Zero-Doppler correlation design: M=2, N=1200, B=16, every delay, the
+    single bin nu = 0, SNRL target 0 dB (the setting of the paper's
+    correlation comparison)."""
+    return Workload("correlation M=2 N=1200 B=16 L=1 (nu=0) full-range", 2, 1200, 16, -1199, 1199,
+                    np.zeros(1), snrl_db=0.0)
+
+
 def small(M: int, N: int, B: int, L: int, k_lo: int | None = None, k_hi: int | None = None,
           r_n: int = 100) -> Workload:
     """A small full-grid case for parity tests."""

@@ -49,7 +49,8 @@ def _evals_per_s(api, ctx, w, seed, matched=False):
 
 
 ROWS = [("tiny", "auto"), ("mid", "auto"), ("precision", "dft"), ("precision", "split"),
-        ("learned", "dft"), ("learned", "split"), ("differentiation", "auto"), ("mid", "sqnaf")]
+        ("learned", "dft"), ("learned", "split"), ("differentiation", "auto"), ("mid", "sqnaf"),
+        ("correlation", "auto"), ("correlation", "split")]
 
 
 @pytest.mark.parametrize("which,path", ROWS)
