@@ -31,6 +31,61 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 // multiply by +j
 template <typename C> __device__ __forceinline__ C cmulj(C a) { return mk(-a.y, a.x); }
 
+// ------------------------------------------------------- double-float sums --
+// A value kept as hi + lo in two FP32 words (|lo| <= ulp(hi)/2).  Sums of
+// FP32 partials in this form keep about 44 significant bits using FP32
+// instructions only.  On this GPU the FP64 pipe is a latency trap on the
+// per-evaluation critical path: a dependent FP64 add or FMA takes about ten
+// times an FP32 one and an FP64 division or square root hundreds of cycles,
+// and its throughput is a few operations per clock per SM.
+struct __align__(8) DFloat {
+    float hi, lo;
+};
+
+// Knuth's TwoSum of the high words (exact: s + e = a.hi + b.hi), then the
+// low words folded in and the result renormalised.  The _rn intrinsics keep
+// the compiler from contracting or reassociating the steps.
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DFloat df_warp_sum(DFloat a) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const DFloat b = {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+        a = df_add(a, b);
+    }
+    return a;
+}
+__device__ __forceinline__ double df_to_double(DFloat a) { return (double)a.hi + (double)a.lo; }
+
+// chi_mm(0, 0) = sum_n x(n) conj(h(n)) (Eq. 38) by the NT threads of a CTA
+// (all of them call it; it synchronises the CTA once): FP32 products and
+// per-thread partials, then a double-float tree; thread 0 stores the sum.
+template <int NT>
+__device__ __forceinline__ void diag_sum_f32(const float2* __restrict__ x, const float2* __restrict__ h, int N,
+                                             double2* out) {
+    __shared__ DFloat red[2][NT / 32];
+    const int tid = threadIdx.x;
+    float sr = 0.f, si = 0.f;
+    for (int n = tid; n < N; n += NT) {
+        const float2 xv = x[n], hv = h[n];
+        sr = fmaf(xv.x, hv.x, fmaf(xv.y, hv.y, sr));
+        si = fmaf(xv.y, hv.x, fmaf(-xv.x, hv.y, si));
+    }
+    const DFloat r = df_warp_sum({sr, 0.f}), i = df_warp_sum({si, 0.f});
+    if ((tid & 31) == 0) { red[0][tid >> 5] = r; red[1][tid >> 5] = i; }
+    __syncthreads();
+    if (tid == 0) {
+        DFloat tr = red[0][0], ti = red[1][0];
+        for (int w = 1; w < NT / 32; ++w) { tr = df_add(tr, red[0][w]); ti = df_add(ti, red[1][w]); }
+        *out = make_double2(df_to_double(tr), df_to_double(ti));
+    }
+}
+
 // e^{+j 2 pi s / 16} for s = 0..7 (cos, sin of multiples of pi/8).
 __device__ __forceinline__ constexpr double w16c(int s) {
     return s == 0 ? 1.0 : s == 1 ? 0.92387953251128675613 : s == 2 ? 0.70710678118654752440

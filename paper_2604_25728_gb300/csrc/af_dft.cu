@@ -49,7 +49,11 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
         xs[n] = a.x[(size_t)m * N + n];
         hs[n] = a.h[(size_t)l * N + n];
     }
-    if (a.cdiag != nullptr && m == l && chunk == 0 && ctile == 0) {
+    if constexpr (sizeof(K) == 4) {
+        // double-float sums in the FP32 instantiation
+        if (a.cdiag != nullptr && m == l && chunk == 0 && ctile == 0)
+            diag_sum_f32<kDftThreads>(a.x + (size_t)m * N, a.h + (size_t)l * N, N, a.cdiag + m);
+    } else if (a.cdiag != nullptr && m == l && chunk == 0 && ctile == 0) {
         double sr = 0.0, si = 0.0;
         for (int n = tid; n < N; n += kDftThreads) {
             C xv = a.x[(size_t)m * N + n], hv = a.h[(size_t)l * N + n];
@@ -215,13 +219,13 @@ fwd_dft_kernel(const FwdArgs<C, K> a) {
 // with x' = x e^{j 2 pi nu_0 n}, a plain cross-correlation.  The tiled DFT
 // above would spend 63 of its 64 bin columns on padding, so this kernel
 // gives each CTA 32 consecutive delays of one pair (lane = delay) and splits
-// the samples n of their common range across the 8 warps.  Shared memory
+// the samples n of their common range across its 16 warps.  Shared memory
 // holds x' and h over that range, relative to its first sample and
 // zero-padded, so lane t at offset i reads x'[i] (one broadcast) and
 // h[i + t] (consecutive words): no bounds checks, no bank conflicts.  The
 // warps' partial sums are added in a fixed order by warp 0, which also
 // runs the sidelobe reduction of its 32 cells.
-constexpr int kCorrThreads = 256;
+constexpr int kCorrThreads = 512;
 constexpr int kCorrWarps = kCorrThreads / 32;
 constexpr int TRC = 32;            // delays per CTA
 constexpr int kCorrPad = 4 * kCorrWarps + TRC;   // extra slots beyond N in each buffer
@@ -263,8 +267,10 @@ fwd_corr_kernel(const FwdArgs<C, K> a) {
         const int p = p_lo + q;
         hs[q] = (p >= 0 && p < N) ? hg[p] : mk((T)0, (T)0);
     }
-    if (a.cdiag != nullptr && m == l && chunk == 0) {
-        // A_mm(0, 0) in FP64 (Eq. 38)
+    // A_mm(0, 0) (Eq. 38): double-float sums in the FP32 instantiation, FP64 in the FP64 one
+    if constexpr (sizeof(K) == 4) {
+        if (a.cdiag != nullptr && m == l && chunk == 0) diag_sum_f32<kCorrThreads>(xg, hg, N, a.cdiag + m);
+    } else if (a.cdiag != nullptr && m == l && chunk == 0) {
         double sr = 0.0, si = 0.0;
         for (int n = tid; n < N; n += kCorrThreads) {
             const C xv = xg[n], hv = hg[n];

@@ -117,8 +117,12 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
         }
     }
 
-    // chi_mm(0, 0) = h_m^H x_m in FP64 (Eq. 38), once per waveform.
-    if (a.cdiag != nullptr && m == l && chunk == 0) {
+    // chi_mm(0, 0) = h_m^H x_m (Eq. 38), once per waveform: double-float sums
+    // in the FP32 instantiation, FP64 in the FP64 one.
+    if constexpr (sizeof(K) == 4) {
+        if (a.cdiag != nullptr && m == l && chunk == 0)
+            diag_sum_f32<kThreads>(a.x + (size_t)m * N, a.h + (size_t)l * N, N, a.cdiag + m);
+    } else if (a.cdiag != nullptr && m == l && chunk == 0) {
         double sr = 0.0, si = 0.0;
         for (int n = tid; n < N; n += kThreads) {
             const C xv = a.x[(size_t)m * N + n], hv = a.h[(size_t)l * N + n];

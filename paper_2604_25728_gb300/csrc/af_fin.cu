@@ -55,15 +55,6 @@ __device__ __forceinline__ float2 cell_phasor(const FinArgs& a, int j, int n) {
     return a.E[(size_t)n * a.L + j];
 }
 
-// sqrt of a non-negative double: FP32 square root refined by one Newton step
-// (relative error ~1e-15), avoiding the long FP64 square-root sequence.
-__device__ __forceinline__ double sqrt_d(double v) {
-    if (!(v > 0.0)) return 0.0;
-    const float s = sqrtf((float)v);
-    const double r = (double)s;
-    return r + (double)((float)fma(-r, r, v) / (2.f * s));
-}
-
 // Element i of thread t of strip s is n = s * blockDim.x + t + i * kFT
 // (EPT = 1: one element per thread).
 template <int EPT, int MODE>
@@ -76,13 +67,13 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     const int NW = blockDim.x >> 5;
     const int M = a.M, N = a.N;
 
-    __shared__ double shd[kNW];
+    __shared__ DFloat shd[kNW];
     __shared__ float sk[2][kNW];
     __shared__ long long si[2][kNW];
     __shared__ float2 sc2[2][kNW];
     __shared__ float spv[2][kNW], sps[2][kNW];
-    __shared__ double s_terms[8];
-    __shared__ double s_pmin2;
+    __shared__ float s_terms[8];
+    __shared__ float s_pmin2;
     __shared__ float2 s_g;           // sparse coefficient g
     __shared__ int s_cell[4];        // m*, l*, k*, j*  (m* = -1: no sparse term)
     __shared__ float2 s_G;           // SNRL coefficient of row m
@@ -90,7 +81,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     __shared__ long long s_ctr[4];
     __shared__ double s_best[8];
     __shared__ int s_ok;
-    __shared__ double s_part;        // this strip's partial ||h||^2 (read by the cluster)
+    __shared__ DFloat s_part;        // this strip's partial ||h||^2 (read by the cluster)
 
     pdl_trigger();
 
@@ -150,8 +141,12 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (ids[u] < 0) continue;
             const int pair = (b0 + u * (int)blockDim.x + tid) / a.ctas_per_pair;
             const int cls = (pair / M == pair % M) ? 0 : 1;
-            if (fbetter(ks[u], ids[u], kb[cls], ib[cls])) { kb[cls] = ks[u]; ib[cls] = ids[u]; cb[cls] = cs[u]; }
-            if (a.half_p > 0.f) pmerge(a.half_p, pv[cls], ps[cls], vv[u], ss[u]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {            // static indices: the class arrays stay in registers
+                if (c != cls) continue;
+                if (fbetter(ks[u], ids[u], kb[c], ib[c])) { kb[c] = ks[u]; ib[c] = ids[u]; cb[c] = cs[u]; }
+                if (a.half_p > 0.f) pmerge(a.half_p, pv[c], ps[c], vv[u], ss[u]);
+            }
         }
     }
 #pragma unroll
@@ -172,31 +167,32 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         }
     }
 
-    // ---- 2. SNRL term, one waveform per lane of warp 0 (FP64); counters -------
+    // ---- 2. SNRL term, one waveform per lane of warp 0 (FP32); counters -------
     if (warp == 0) {
-        double p = 0.0, c2 = 0.0;
-        if (lane < M) {
-            c2 = cm.x * cm.x + cm.y * cm.y;
-            p = sqrt_d(c2) * a.inv_N;                      // p_m = |A_mm(0,0)| / N (Eq. 38)
-        }
-        const double dev = p - a.ptar;
-        double ls = (lane < M) ? dev * dev : 0.0;
-        double pmin2 = (lane < M) ? c2 * a.inv_N * a.inv_N : 1e300;
+        // A_mm(0,0) arrives as a double-float sum; p_m and L_SNRL need no more
+        // than FP32 (relative error ~1e-7), and FP64 here would put dependent
+        // FP64 operations on every evaluation's critical path
+        const float cr = (float)cm.x, ci = (float)cm.y;
+        const float c2 = cr * cr + ci * ci;
+        const float p = (lane < M) ? sqrtf(c2) * a.inv_N_f : 0.f;   // p_m = |A_mm(0,0)| / N (Eq. 38)
+        const float dev = p - a.ptar_f;
+        float ls = (lane < M) ? dev * dev : 0.f;
+        float pmin2 = (lane < M) ? c2 * a.inv_N_f * a.inv_N_f : 3.0e38f;
         for (int o = 16; o > 0; o >>= 1) {
             ls += __shfl_xor_sync(0xffffffffu, ls, o);
-            pmin2 = fmin(pmin2, __shfl_xor_sync(0xffffffffu, pmin2, o));
+            pmin2 = fminf(pmin2, __shfl_xor_sync(0xffffffffu, pmin2, o));
         }
         if (lane == m) {
             // G_m = (1-eps)(2/M)(p_m - p_tar)/N * c_m/|c_m|
-            const float mag = (float)(p * (double)N);
-            const float coef = (mag > 0.f) ? (float)(a.snrl_coef * dev) / mag : 0.f;
-            s_G = make_float2(coef * (float)cm.x, coef * (float)cm.y);
+            const float mag = p * (float)N;
+            const float coef = (mag > 0.f) ? a.snrl_coef_f * dev / mag : 0.f;
+            s_G = make_float2(coef * cr, coef * ci);
         }
         if (lane == 0) {
-            s_terms[4] = ls / (double)M;                   // L_SNRL (Eq. 41)
+            s_terms[4] = ls * a.inv_M_f;                   // L_SNRL (Eq. 41)
             s_pmin2 = pmin2;
         }
-        if (m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = p;
+        if (m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = (double)p;
     } else if (warp == 1 && opt) {
         if (lane == 0) {
             s_ctr[0] = cv0; s_ctr[1] = cv1; s_ctr[2] = cv2; s_ctr[3] = cv3;
@@ -212,9 +208,10 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
 
     // ---- 3. class values, loss, winning cell, best-design record --------------
     if (tid == 0) {
-        double cvv[2];
+        float cvv[2];
         long long cell[2];
         float2 chi[2];
+#pragma unroll
         for (int c = 0; c < 2; ++c) {
             float k = sk[c][0];
             long long i = si[c][0];
@@ -224,25 +221,26 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 if (fbetter(sk[c][w], si[c][w], k, i)) { k = sk[c][w]; i = si[c][w]; x = sc2[c][w]; }
                 if (a.half_p > 0.f) pmerge(a.half_p, v, sm, spv[c][w], sps[c][w]);
             }
-            const double wscale = (a.weight_mode == WM_UNIFORM) ? (double)a.w0 : 1.0;
+            const float wscale = (a.weight_mode == WM_UNIFORM) ? a.w0 : 1.f;
             const bool any = (k >= 0.f) && (i != 0x7fffffffffffffffLL);
             cell[c] = any ? i : -1;
             chi[c] = x;
-            if (!any) cvv[c] = 0.0;
-            else if (a.half_p > 0.f) cvv[c] = wscale * (double)(sqrtf(v) * powf(sm, 0.5f / a.half_p));
-            else cvv[c] = wscale * (double)sqrtf(k);
+            if (!any) cvv[c] = 0.f;
+            else if (a.half_p > 0.f) cvv[c] = wscale * (sqrtf(v) * powf(sm, 0.5f / a.half_p));
+            else cvv[c] = wscale * sqrtf(k);
         }
         const int cls = (cvv[0] >= cvv[1]) ? 0 : 1;
-        const double lw = cvv[cls];
-        const double ls = s_terms[4];
-        s_terms[0] = a.eps * lw + (1.0 - a.eps) * ls;      // Eq. 42
+        const float lw = cls ? cvv[1] : cvv[0];
+        const long long cell_w = cls ? cell[1] : cell[0];
+        const float2 chi_w = cls ? chi[1] : chi[0];
+        const float ls = s_terms[4];
+        s_terms[0] = a.eps_f * lw + (1.f - a.eps_f) * ls;   // Eq. 42
         s_terms[1] = lw; s_terms[2] = cvv[0]; s_terms[3] = cvv[1];
-        s_terms[5] = (double)cls; s_terms[6] = (double)cell[0]; s_terms[7] = (double)cell[1];
         // winning cell of the exact max and its coefficient g = eps w chi/|chi|
         s_cell[0] = -1;
         s_g = zero2;
-        if (a.half_p <= 0.f && cell[cls] >= 0) {
-            const long long cc = cell[cls];
+        if (a.half_p <= 0.f && cell_w >= 0) {
+            const long long cc = cell_w;
             int j, d, pair;
             if (cc < 0x7fffffffLL) {
                 const unsigned c32 = (unsigned)cc, L32 = (unsigned)a.L, D32 = (unsigned)a.D;
@@ -256,20 +254,23 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 pair = (int)(cc / ((long long)a.L * a.D));
             }
             s_cell[0] = pair / M; s_cell[1] = pair % M; s_cell[2] = a.k_lo + d; s_cell[3] = j;
-            const float cr = chi[cls].x, ci = chi[cls].y;
+            const float cr = chi_w.x, ci = chi_w.y;
             const float mag = sqrtf(cr * cr + ci * ci);
             const float w = (a.weight_mode == WM_UNIFORM) ? a.w0 : a.wmap[(size_t)d * a.L + j];
             if (mag > 0.f) {
-                const float f = (float)a.eps * w / mag;
+                const float f = a.eps_f * w / mag;
                 s_g = make_float2(f * cr, f * ci);
             }
         }
         const long long o = opt ? s_ctr[0] - 1 : 0;
         if (m == 0 && blockIdx.x == 0) {
-            if (a.terms) for (int i = 0; i < 8; ++i) a.terms[i] = s_terms[i];
+            if (a.terms) {
+                for (int i = 0; i < 5; ++i) a.terms[i] = (double)s_terms[i];
+                a.terms[5] = (double)cls; a.terms[6] = (double)cell[0]; a.terms[7] = (double)cell[1];
+            }
             if (a.log) {
                 double* lg = a.log + ((size_t)o * a.evals_per_outer + a.eval_index) * 4;
-                lg[0] = s_terms[0]; lg[1] = s_terms[1]; lg[2] = s_terms[4]; lg[3] = s_terms[5];
+                lg[0] = (double)s_terms[0]; lg[1] = (double)lw; lg[2] = (double)ls; lg[3] = (double)cls;
             }
             if (!isfinite(s_terms[0]) && a.err_flag) atomicOr(a.err_flag, 1);
         }
@@ -280,11 +281,11 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 const double* prev = s_best + ((o + 1) & 1) * 4;
                 double* cur = a.best2 + (o & 1) * 4;
                 // SNRL_m = -20 log10 p_m <= target + 0.05 dB  <=>  p_m^2 >= p_accept2
-                s_ok = (s_pmin2 >= a.p_accept2 && s_terms[1] < prev[0]) ? 1 : 0;
+                s_ok = (s_pmin2 >= a.p_accept2_f && (double)lw < prev[0]) ? 1 : 0;
                 if (m == 0 && blockIdx.x == 0) {
                     if (s_ok) {
-                        cur[0] = s_terms[1]; cur[1] = s_terms[0];
-                        cur[2] = (double)(s_ctr[3] + o); cur[3] = (double)(-10.f * log10f((float)s_pmin2));
+                        cur[0] = (double)lw; cur[1] = (double)s_terms[0];
+                        cur[2] = (double)(s_ctr[3] + o); cur[3] = (double)(-10.f * log10f(s_pmin2));
                     } else {
                         for (int i = 0; i < 4; ++i) cur[i] = prev[i];
                     }
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     if (MODE == FIN_ADAM_H) {
         // Adam on (H_Re, H_Im), then the projection of Eq. 32 with the row's norm
         float2 hv[EPT];
-        double e2 = 0.0;
+        float e2 = 0.f;
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
             const int n = n_base + tid + i * kFT;
@@ -385,22 +386,30 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             a.m_h[e] = mm_;
             a.v_h[e] = vv;
             hv[i] = h_;
-            e2 += (double)h_.x * h_.x + (double)h_.y * h_.y;
+            e2 = fmaf(h_.x, h_.x, fmaf(h_.y, h_.y, e2));
         }
-        const double part = block_sum_d(e2, shd);
-        if (tid == 0) s_part = part;
+        // ||h_m||^2 as a double-float tree: warps, then the strips of the cluster
+        const DFloat wsum = df_warp_sum({e2, 0.f});
+        if (lane == 0) shd[warp] = wsum;
+        __syncthreads();
+        if (tid == 0) {
+            DFloat t = shd[0];
+            for (int w = 1; w < NW; ++w) t = df_add(t, shd[w]);
+            s_part = t;
+        }
         tc::cluster_sync();                          // every strip's partial is in place
-        double tot = 0.0;
+        DFloat tot = {0.f, 0.f};
         const uint32_t local = tc::smem_u32(&s_part);
         for (int r = 0; r < S; ++r) {
             uint32_t remote;
-            double v;
+            DFloat v;
             asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
-            asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
-            tot += v;
+            asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.hi), "=f"(v.lo) : "r"(remote) : "memory");
+            tot = df_add(tot, v);
         }
         tc::cluster_sync();                          // no CTA leaves while its partial may be read
-        const float sc = (tot > 0.0) ? (float)sqrt_d((double)N / tot) : 1.f;
+        const float tf = tot.hi + tot.lo;
+        const float sc = (tf > 0.f) ? sqrtf((float)N / tf) : 1.f;
         bad |= !isfinite(sc);
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
@@ -463,7 +472,14 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     }
 }
 
-cudaError_t launch_fin(const FinArgs& a, cudaStream_t s) {
+cudaError_t launch_fin(const FinArgs& a_in, cudaStream_t s) {
+    FinArgs a = a_in;
+    a.eps_f = (float)a.eps;
+    a.ptar_f = (float)a.ptar;
+    a.inv_N_f = (float)a.inv_N;
+    a.snrl_coef_f = (float)a.snrl_coef;
+    a.inv_M_f = (float)(1.0 / a.M);
+    a.p_accept2_f = (float)a.p_accept2;
     const int T = fin_threads(a.N);
     const int S = (a.N + T - 1) / T;
     if (S > kMaxStrips) return cudaErrorInvalidValue;   // N > 4096 is rejected by the host checks

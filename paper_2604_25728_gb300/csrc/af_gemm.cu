@@ -141,7 +141,7 @@ fwd_gemm_kernel(const GemmArgs g) {
     __shared__ float rk[T][4];
     __shared__ long long ri[T][4];
     __shared__ float2 rc[T][4];
-    __shared__ double red[T][2][4];
+    __shared__ DFloat red[T][2][4];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -306,11 +306,11 @@ fwd_gemm_kernel(const GemmArgs g) {
                 if (i < nx) xs[i] = xv[q];
             }
         }
-        // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) in FP64 (SNRL, Eq. 38), while
-        // the first B stages are still in flight
+        // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) (SNRL, Eq. 38) while the first
+        // B stages are still in flight: FP32 products and partials, double-float tree
         if (a.cdiag != nullptr && tile == 0 && ct == 0) {
             const bool diag = (m == l);
-            double sr = 0.0, si = 0.0;
+            float sr = 0.f, si = 0.f;
             if (diag) {
                 for (int n0 = r; n0 < N; n0 += kTM * FB) {
                     float2 xv[FB], hv[FB];
@@ -322,21 +322,19 @@ fwd_gemm_kernel(const GemmArgs g) {
                     }
 #pragma unroll
                     for (int q = 0; q < FB; ++q) {
-                        const double xr = xv[q].x, xi = xv[q].y, hr = hv[q].x, hi_ = hv[q].y;
-                        sr += xr * hr + xi * hi_;
-                        si += xi * hr - xr * hi_;
+                        sr = fmaf(xv[q].x, hv[q].x, fmaf(xv[q].y, hv[q].y, sr));
+                        si = fmaf(xv[q].y, hv[q].x, fmaf(-xv[q].x, hv[q].y, si));
                     }
                 }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                si += __shfl_xor_sync(0xffffffffu, si, o);
-            }
-            if (lane == 0) { red[t][0][warp & 3] = sr; red[t][1][warp & 3] = si; }
+            const DFloat dr = df_warp_sum({sr, 0.f}), di = df_warp_sum({si, 0.f});
+            if (lane == 0) { red[t][0][warp & 3] = dr; red[t][1][warp & 3] = di; }
             asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
-            if (diag && r == 0)
-                a.cdiag[m] = make_double2(red[t][0][0] + red[t][0][1] + red[t][0][2] + red[t][0][3],
-                                          red[t][1][0] + red[t][1][1] + red[t][1][2] + red[t][1][3]);
+            if (diag && r == 0) {
+                DFloat tr = red[t][0][0], ti = red[t][1][0];
+                for (int w = 1; w < 4; ++w) { tr = df_add(tr, red[t][0][w]); ti = df_add(ti, red[t][1][w]); }
+                a.cdiag[m] = make_double2(df_to_double(tr), df_to_double(ti));
+            }
         }
         asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
 

@@ -85,6 +85,8 @@ struct FinArgs {
     double snrl_db;
     double p_accept2;         // (10^{-(snrl_db + 0.05)/20})^2: a design is acceptable when min p_m^2 >= this
     int matched;              // SQNAF: h = x, the gradient of x is the sum of both partials
+    // FP32 copies of the double constants above, filled by launch_fin
+    float eps_f, ptar_f, inv_N_f, snrl_coef_f, inv_M_f, p_accept2_f;
 };
 
 struct AccArgs {
