@@ -28,15 +28,26 @@ __device__ __forceinline__ int upper_bound_f(const float* v, int n, float x) {
     return lo;
 }
 
-// Number of thresholds <= v (upper bound).  For the uniform set
-// rho_i = (i + 1/2)/K the answer is within one of floor(K v + 1/2); the table
-// is then consulted at most twice, so the count is exact for any v.
+// Threshold i of the uniform set rho_i = (i + 1/2)/K, bit-identical to the
+// table the host builds as the FP32 rounding of the FP64 quotient: the exact
+// value (2i+1)/(2K) has 2K <= 2^21, so it lies at least 2^-45 (relative)
+// away from any FP32 rounding boundary it does not sit on, and it sits on one
+// only if it is a dyadic fraction of at most 21 bits (then it is exact).  The
+// FP64 rounding therefore cannot move it across a boundary, and the FP32
+// division of the exact operands 2i+1 and 2K returns the same float.
+__device__ __forceinline__ float rho_uniform(int i, int K) {
+    return __fdiv_rn((float)(2 * i + 1), (float)(2 * K));
+}
+
+// Number of thresholds <= v (upper bound).  For the uniform set the answer is
+// within one of floor(K v + 1/2); one or two thresholds, computed as the table
+// holds them, settle it, so the count is exact for any v and reads no memory.
 __device__ __forceinline__ int count_le(const QuantArgs& q, float v) {
     if (!q.uniform) return upper_bound_f(q.rho, q.K, v);
     int c = (int)floorf(fminf(fmaxf(v, -1.f), 2.f) * (float)q.K + 0.5f);
     c = min(max(c, 0), q.K);
-    if (c > 0 && __ldg(q.rho + c - 1) > v) --c;
-    else if (c < q.K && __ldg(q.rho + c) <= v) ++c;
+    if (c > 0 && rho_uniform(c - 1, q.K) > v) --c;
+    else if (c < q.K && rho_uniform(c, q.K) <= v) ++c;
     return c;
 }
 // Number of thresholds < v (lower bound), same scheme.
@@ -44,8 +55,8 @@ __device__ __forceinline__ int count_lt(const QuantArgs& q, float v) {
     if (!q.uniform) return lower_bound_f(q.rho, q.K, v);
     int c = (int)ceilf(fminf(fmaxf(v, -1.f), 2.f) * (float)q.K - 0.5f);
     c = min(max(c, 0), q.K);
-    if (c > 0 && __ldg(q.rho + c - 1) >= v) --c;
-    else if (c < q.K && __ldg(q.rho + c) < v) ++c;
+    if (c > 0 && rho_uniform(c - 1, q.K) >= v) --c;
+    else if (c < q.K && rho_uniform(c, q.K) < v) ++c;
     return c;
 }
 
@@ -70,21 +81,32 @@ __device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, fl
             const float c2 = 2.f * q.c;
             const float r_up = expf(-c2 * invK);         // e_{i+1} / e_i
             const float r_dn = expf(c2 * invK);          // e_{i-1} / e_i
-            float sum_inv = 0.f, sum_d = 0.f;            // sum 1/(1+e), sum e/(1+e)^2
-            float e = expf(c2 * (z - ((float)ic + 0.5f) * invK));
-            for (int i = ic; i < i1; ++i) {
-                const float inv = __frcp_rn(1.f + e);
-                sum_inv += inv;
-                sum_d = fmaf(e * inv, inv, sum_d);
-                e *= r_up;
+            const float r_up2 = r_up * r_up, r_dn2 = r_dn * r_dn;
+            // four interleaved chains (two upward from ic, two downward from
+            // ic - 1), each stepping two thresholds, so the in-order pipeline
+            // always has independent work; terms past either end of the window
+            // are masked out.  1/(1+e) uses the hardware reciprocal (~1 ulp):
+            // e -> inf gives 0 and e -> 0 gives 1, the saturated limits.
+            float eu0 = expf(c2 * (z - ((float)ic + 0.5f) * invK));
+            float ed0 = expf(c2 * (z - ((float)ic - 0.5f) * invK));
+            float eu1 = eu0 * r_up, ed1 = ed0 * r_dn;
+            const int n_up = i1 - ic, n_dn = ic - i0;
+            const int n_it = max(n_up, n_dn);
+            float si0 = 0.f, si1 = 0.f, si2 = 0.f, si3 = 0.f;   // sum 1/(1+e)
+            float sd0 = 0.f, sd1 = 0.f, sd2 = 0.f, sd3 = 0.f;   // sum e/(1+e)^2
+            for (int t = 0; t < n_it; t += 2) {
+                // past its end a downward chain may overflow to inf: selects, not
+                // multiplications by 0, keep those terms out
+                const float i0_ = __fdividef(1.f, 1.f + eu0), i1_ = __fdividef(1.f, 1.f + eu1);
+                const float i2_ = __fdividef(1.f, 1.f + ed0), i3_ = __fdividef(1.f, 1.f + ed1);
+                if (t < n_up) { si0 += i0_; sd0 = fmaf(eu0 * i0_, i0_, sd0); }
+                if (t + 1 < n_up) { si1 += i1_; sd1 = fmaf(eu1 * i1_, i1_, sd1); }
+                if (t < n_dn) { si2 += i2_; sd2 = fmaf(ed0 * i2_, i2_, sd2); }
+                if (t + 1 < n_dn) { si3 += i3_; sd3 = fmaf(ed1 * i3_, i3_, sd3); }
+                eu0 *= r_up2; eu1 *= r_up2; ed0 *= r_dn2; ed1 *= r_dn2;
             }
-            e = expf(c2 * (z - ((float)ic - 0.5f) * invK));
-            for (int i = ic - 1; i >= i0; --i) {
-                const float inv = __frcp_rn(1.f + e);
-                sum_inv += inv;
-                sum_d = fmaf(e * inv, inv, sum_d);
-                e *= r_dn;
-            }
+            const float sum_inv = (si0 + si1) + (si2 + si3);
+            const float sum_d = (sd0 + sd1) + (sd2 + sd3);
             // sum a (tanh + 1) = a (2 W - 2 sum_inv);  sum a c (1 - tanh^2) = 4 a c sum_d
             s = 2.f * q.a * ((float)(i1 - i0) - sum_inv);
             ds = 4.f * q.a * q.c * sum_d;

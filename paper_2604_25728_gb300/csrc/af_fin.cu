@@ -85,6 +85,20 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
 
     pdl_trigger();
 
+    // The body runs twice from one copy of its code.  Pass 0 is a dry run
+    // made while the forward pass is still running: it computes on whatever
+    // the workspace holds, clamps every index it derives from it and stores
+    // nothing, and so brings this kernel's instructions and parameters into
+    // the SM's caches.  Each launch otherwise meets them cold, and its
+    // straight-line code ran about a third slower for it (measured: 9.3 us
+    // cold against 5.9 us warm from the dependency wait to the end).  Pass 1
+    // waits for the forward pass and does the work.  Data the forward pass
+    // writes is loaded with __ldcg (L2 only), so pass 1 never sees a line
+    // that pass 0 left in L1 before the forward pass had written it.
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+    const bool dry = (pass == 0);
+
     // ---- 0. this row's inputs (not written by the forward pass) ---------------
     const float2 zero2 = make_float2(0.f, 0.f);
     float2 xm[EPT], hm[EPT], mh[EPT], vh[EPT];
@@ -104,18 +118,18 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (MODE == FIN_GRAD_U && a.grad_u != nullptr) { uu[i] = a.u[e]; dy[i] = a.dydz[e]; }
         }
     }
-    pdl_wait();
+    if (!dry) pdl_wait();
 
     // ---- 1. one batch of loads of everything the previous kernels wrote -------
     double2 cm = make_double2(0.0, 0.0);
-    if (warp == 0 && lane < M) cm = a.cdiag[lane];
+    if (warp == 0 && lane < M) cm = __ldcg(a.cdiag + lane);
     constexpr bool kSnap = (MODE == FIN_ADAM_H || MODE == FIN_SCORE);   // may take the best-design record
     const bool opt = (MODE == FIN_ADAM_H || MODE == FIN_ADAM_U || MODE == FIN_SCORE) && a.ctr != nullptr;
     long long cv0 = 0, cv1 = 0, cv2 = 0, cv3 = 0;
     double bv = 0.0;
     if (warp == 1 && opt) {
-        if (lane == 0) { cv0 = a.ctr[0]; cv1 = a.ctr[1]; cv2 = a.ctr[2]; cv3 = a.ctr[3]; }
-        if (kSnap && a.snap_best && lane < 8) bv = a.best2[lane];
+        if (lane == 0) { cv0 = __ldcg(a.ctr); cv1 = __ldcg(a.ctr + 1); cv2 = __ldcg(a.ctr + 2); cv3 = __ldcg(a.ctr + 3); }
+        if (kSnap && a.snap_best && lane < 8) bv = __ldcg(a.best2 + lane);
     }
     float kb[2] = {-1.f, -1.f};
     long long ib[2] = {0x7fffffffffffffffLL, 0x7fffffffffffffffLL};
@@ -130,11 +144,11 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         for (int u = 0; u < U; ++u) {
             const int b = b0 + u * (int)blockDim.x + tid;
             const bool ok = b < a.nblk;
-            ids[u] = ok ? a.pidx[b] : -1;
-            ks[u] = ok ? a.pkey[b] : -1.f;
-            cs[u] = ok ? a.pchi[b] : zero2;
-            vv[u] = (ok && a.half_p > 0.f) ? a.pvmax[b] : 0.f;
-            ss[u] = (ok && a.half_p > 0.f) ? a.psum[b] : 0.f;
+            ids[u] = ok ? __ldcg(a.pidx + b) : -1;
+            ks[u] = ok ? __ldcg(a.pkey + b) : -1.f;
+            cs[u] = ok ? __ldcg(a.pchi + b) : zero2;
+            vv[u] = (ok && a.half_p > 0.f) ? __ldcg(a.pvmax + b) : 0.f;
+            ss[u] = (ok && a.half_p > 0.f) ? __ldcg(a.psum + b) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -192,7 +206,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             s_terms[4] = ls * a.inv_M_f;                   // L_SNRL (Eq. 41)
             s_pmin2 = pmin2;
         }
-        if (m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = (double)p;
+        if (!dry && m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = (double)p;
     } else if (warp == 1 && opt) {
         if (lane == 0) {
             s_ctr[0] = cv0; s_ctr[1] = cv1; s_ctr[2] = cv2; s_ctr[3] = cv3;
@@ -253,6 +267,11 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 d = (int)((cc / a.L) % a.D);
                 pair = (int)(cc / ((long long)a.L * a.D));
             }
+            if (dry) {                                 // workspace contents may be anything
+                pair = min(max(pair, 0), M * M - 1);
+                d = min(max(d, 0), a.D - 1);
+                j = min(max(j, 0), a.L - 1);
+            }
             s_cell[0] = pair / M; s_cell[1] = pair % M; s_cell[2] = a.k_lo + d; s_cell[3] = j;
             const float cr = chi_w.x, ci = chi_w.y;
             const float mag = sqrtf(cr * cr + ci * ci);
@@ -263,7 +282,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             }
         }
         const long long o = opt ? s_ctr[0] - 1 : 0;
-        if (m == 0 && blockIdx.x == 0) {
+        if (!dry && m == 0 && blockIdx.x == 0) {
             if (a.terms) {
                 for (int i = 0; i < 5; ++i) a.terms[i] = (double)s_terms[i];
                 a.terms[5] = (double)cls; a.terms[6] = (double)cell[0]; a.terms[7] = (double)cell[1];
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 double* cur = a.best2 + (o & 1) * 4;
                 // SNRL_m = -20 log10 p_m <= target + 0.05 dB  <=>  p_m^2 >= p_accept2
                 s_ok = (s_pmin2 >= a.p_accept2_f && (double)lw < prev[0]) ? 1 : 0;
-                if (m == 0 && blockIdx.x == 0) {
+                if (!dry && m == 0 && blockIdx.x == 0) {
                     if (s_ok) {
                         cur[0] = (double)lw; cur[1] = (double)s_terms[0];
                         cur[2] = (double)(s_ctr[3] + o); cur[3] = (double)(-10.f * log10f(s_pmin2));
@@ -330,8 +349,8 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 const size_t e = (size_t)m * N + n;
                 for (int b = 0; b < a.n_dense; ++b) {
                     const float2* base = a.dense_g + (size_t)b * 2 * M * N;
-                    if (need_gx) gx[i] = cadd(gx[i], base[e]);
-                    if (need_gh) gh[i] = cadd(gh[i], base[(size_t)M * N + e]);
+                    if (need_gx) gx[i] = cadd(gx[i], __ldcg(base + e));
+                    if (need_gh) gh[i] = cadd(gh[i], __ldcg(base + (size_t)M * N + e));
                 }
             }
             if (a.matched) gx[i] = cadd(gx[i], gh[i]);
@@ -347,6 +366,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (n >= N) continue;
             const size_t e = (size_t)m * N + n;
             bad |= !isfinite(gx[i].x) || !isfinite(gx[i].y) || !isfinite(gh[i].x) || !isfinite(gh[i].y);
+            if (dry) continue;
             if (a.grad_x) a.grad_x[e] = gx[i];
             if (a.grad_h) a.grad_h[e] = gh[i];
             if (MODE == FIN_GRAD_U && a.grad_u != nullptr) {
@@ -357,8 +377,8 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 bad |= !isfinite(gu);
             }
         }
-        if (bad && a.err_flag) atomicOr(a.err_flag, 1);
-        return;
+        if (!dry && bad && a.err_flag) atomicOr(a.err_flag, 1);
+        continue;
     }
 
     const float c1 = s_adam[0], c2 = s_adam[1];
@@ -372,7 +392,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             hv[i] = zero2;
             if (n >= N) continue;
             const size_t e = (size_t)m * N + n;
-            if (a.snap_best && s_ok) {
+            if (!dry && a.snap_best && s_ok) {
                 if (a.best_h) a.best_h[e] = hm[i];
                 if (a.best_q) a.best_q[e] = hard_q(a.qa, sigmoidf_(uu[i]));
             }
@@ -383,8 +403,10 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             vv.y = a.b2 * vv.y + (1.f - a.b2) * gh[i].y * gh[i].y;
             h_.x -= a.lr * (mm_.x / c1) / (sqrtf(vv.x / c2) + a.adam_eps);
             h_.y -= a.lr * (mm_.y / c1) / (sqrtf(vv.y / c2) + a.adam_eps);
-            a.m_h[e] = mm_;
-            a.v_h[e] = vv;
+            if (!dry) {
+                a.m_h[e] = mm_;
+                a.v_h[e] = vv;
+            }
             hv[i] = h_;
             e2 = fmaf(h_.x, h_.x, fmaf(h_.y, h_.y, e2));
         }
@@ -416,12 +438,12 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             const int n = n_base + tid + i * kFT;
             if (n >= N) continue;
             const float2 hp = make_float2(hv[i].x * sc, hv[i].y * sc);
-            a.h[(size_t)m * N + n] = hp;
+            if (!dry) a.h[(size_t)m * N + n] = hp;
             bad |= !isfinite(hp.x) || !isfinite(hp.y);
         }
     } else if (MODE == FIN_SCORE) {
         // the scored design is (X_hard, X_hard): record it if it is the best so far
-        if (a.snap_best && s_ok) {
+        if (!dry && a.snap_best && s_ok) {
 #pragma unroll
             for (int i = 0; i < EPT; ++i) {
                 const int n = n_base + tid + i * kFT;
@@ -443,13 +465,15 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             const float mm_ = a.b1 * mu[i] + (1.f - a.b1) * gg;
             const float vv = a.b2 * vu[i] + (1.f - a.b2) * gg * gg;
             uu[i] -= a.lr * (mm_ / c1) / (sqrtf(vv / c2) + a.adam_eps);
-            a.m_u[e] = mm_;
-            a.v_u[e] = vv;
-            a.u[e] = uu[i];
+            if (!dry) {
+                a.m_u[e] = mm_;
+                a.v_u[e] = vv;
+                a.u[e] = uu[i];
+            }
             bad |= !isfinite(uu[i]);
         }
     }
-    if (bad && a.err_flag) atomicOr(a.err_flag, 1);
+    if (!dry && bad && a.err_flag) atomicOr(a.err_flag, 1);
 
     // waveform of the next evaluation (depends on u alone)
     if (a.next_wave != NEXT_NONE) {
@@ -460,16 +484,20 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             const size_t e = (size_t)m * N + n;
             const float z = sigmoidf_((MODE == FIN_ADAM_U) ? uu[i] : a.u[e]);
             if (a.next_wave == NEXT_HARD) {
-                a.x_next[e] = a.qa.level[hard_q(a.qa, z) % a.qa.B];
+                const float2 xv = a.qa.level[hard_q(a.qa, z) % a.qa.B];
+                if (!dry) a.x_next[e] = xv;
             } else {
                 float2 xv;
                 float d;
                 soft_q(a.qa, z, nullptr, &d, &xv);
-                a.x_next[e] = xv;
-                a.dydz_next[e] = d;
+                if (!dry) {
+                    a.x_next[e] = xv;
+                    a.dydz_next[e] = d;
+                }
             }
         }
     }
+    }  // pass
 }
 
 cudaError_t launch_fin(const FinArgs& a_in, cudaStream_t s) {

@@ -149,6 +149,7 @@ struct af_ctx {
     long long* pidx64 = nullptr;
     double2* cdiag = nullptr;
     float2* xs = nullptr;      // soft waveform
+    float2* xs2 = nullptr;     // second soft buffer (matched mode: x_{j+1} is written while x_j is gathered)
     float* dydz = nullptr;
     float2* xh = nullptr;      // hard waveform
     double2* x64 = nullptr;
@@ -220,7 +221,7 @@ static QuantArgs quant_args(const af_ctx* c) {
 static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
-                    c->xs, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
+                    c->xs, c->xs2, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
                     c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->dense,
                     c->bimg};
     for (void* p : ptrs)
@@ -501,6 +502,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         (s = dalloc(c, &c->pchi, c->nblk)) ||
         (s = dalloc(c, &c->pkey64, c->acc_nblk)) || (s = dalloc(c, &c->pidx64, c->acc_nblk)) ||
         (s = dalloc(c, &c->cdiag, M)) || (s = dalloc(c, &c->xs, MN)) || (s = dalloc(c, &c->dydz, MN)) ||
+        (cfg->matched && (s = dalloc(c, &c->xs2, MN))) ||
         (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
         (s = dalloc(c, &c->acc_out, 4 + M)) || (s = dalloc(c, &c->terms_scratch, AF_TERMS_FIXED + M)) ||
         (s = dalloc(c, &c->errflag, 1)) || (s = dalloc(c, &c->ctr, 4)) || (s = dalloc(c, &c->best2, 8)))
@@ -804,18 +806,22 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
         CK(c, launch_fin(f, s));
     }
     for (int j = 0; j < nx; ++j) {
-        const float2* hx = matched ? c->xs : h;
-        CK(c, launch_eval_forward(c, c->xs, hx, s, first ? c->ctr : nullptr));
+        // matched: the filters are this evaluation's waveforms, which other rows
+        // gather while the next waveforms are written, so the two alternate buffers
+        float2* xj = (matched && (j & 1)) ? c->xs2 : c->xs;
+        float2* xn = (matched && !(j & 1)) ? c->xs2 : c->xs;
+        const float2* hx = matched ? xj : h;
+        CK(c, launch_eval_forward(c, xj, hx, s, first ? c->ctr : nullptr));
         first = false;
         FinArgs f = fin_args(c);
         f.mode = FIN_ADAM_U;
-        f.x = c->xs; f.dydz = c->dydz; f.h_in = hx;
+        f.x = xj; f.dydz = c->dydz; f.h_in = hx;
         f.u = st->u_dev; f.m_u = st->m_u_dev; f.v_u = st->v_u_dev;
         f.lr = (float)c->cfg.lr_x;
         f.ctr = c->ctr; f.inner = j;
         f.log = c->log; f.eval_index = (matched ? 1 : nh) + j;
         f.next_wave = (j == nx - 1) ? NEXT_HARD : NEXT_SOFT;
-        f.x_next = (j == nx - 1) ? c->xh : c->xs;
+        f.x_next = (j == nx - 1) ? c->xh : xn;
         f.dydz_next = c->dydz;
         CK(c, launch_fin(f, s));
     }
