@@ -19,6 +19,8 @@
 // per (pair, delay) row, which is the form that keeps every operand on chip.
 #include <stdlib.h>
 
+#include <type_traits>
+
 #include "af_common.cuh"
 #include "af_kernels.h"
 
@@ -191,24 +193,32 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
             }
         } else if (row_in && !(auto_pair && k == 0)) {
             const int lbase = (d - d_begin) * L + t;
-            const float* wrow = (a.weight_mode != WM_UNIFORM) ? a.wmap + (size_t)d * L + t : nullptr;
+            // The weighted scan is a separate copy of the loop: with the weight
+            // test inside the unrolled loop the uniform path's instructions are
+            // interleaved with the weighted ones and the hot loop spans twice
+            // the instruction-cache lines.
+            auto scan = [&](auto weighted) {
+                const float* wrow = a.wmap + (size_t)d * L + t;
 #pragma unroll
-            for (int r = 0; r < RL; ++r) {
+                for (int r = 0; r < RL; ++r) {
 #pragma unroll
-                for (int s = 0; s < NBL; ++s) {
-                    const int off = TPR * s + r * NSL;
-                    const C c = v[s * RL + r];
-                    K key = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
-                    if (wrow != nullptr) {
-                        const float w = __ldg(wrow + off);
-                        key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
-                    }
-                    if (key > best) { best = key; best_li = lbase + off; best_c = c; }
-                    if constexpr (MODE == MODE_REDUCE_PNORM) {
-                        if (key >= (K)0) pnorm_add(a.half_p, (float)key, pv, ps);
+                    for (int s = 0; s < NBL; ++s) {
+                        const int off = TPR * s + r * NSL;
+                        const C c = v[s * RL + r];
+                        K key = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
+                        if constexpr (decltype(weighted)::value) {
+                            const float w = __ldg(wrow + off);
+                            key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
+                        }
+                        if (key > best) { best = key; best_li = lbase + off; best_c = c; }
+                        if constexpr (MODE == MODE_REDUCE_PNORM) {
+                            if (key >= (K)0) pnorm_add(a.half_p, (float)key, pv, ps);
+                        }
                     }
                 }
-            }
+            };
+            if (a.weight_mode == WM_UNIFORM) scan(std::false_type{});
+            else scan(std::true_type{});
         }
     }
 

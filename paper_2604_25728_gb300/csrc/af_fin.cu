@@ -57,7 +57,10 @@ __device__ __forceinline__ float2 cell_phasor(const FinArgs& a, int j, int n) {
 
 // Element i of thread t of strip s is n = s * blockDim.x + t + i * kFT
 // (EPT = 1: one element per thread).
-template <int EPT, int MODE>
+// PN: the p-norm loss (half_p > 0).  A separate instantiation keeps the
+// p-norm merges out of the exact-max code, whose size matters: the kernel
+// runs once per evaluation and waits on instruction fetch.
+template <int EPT, int MODE, bool PN>
 __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     const int m = blockIdx.y;
     const int S = gridDim.x;
@@ -147,8 +150,8 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             ids[u] = ok ? __ldcg(a.pidx + b) : -1;
             ks[u] = ok ? __ldcg(a.pkey + b) : -1.f;
             cs[u] = ok ? __ldcg(a.pchi + b) : zero2;
-            vv[u] = (ok && a.half_p > 0.f) ? __ldcg(a.pvmax + b) : 0.f;
-            ss[u] = (ok && a.half_p > 0.f) ? __ldcg(a.psum + b) : 0.f;
+            vv[u] = (PN && ok) ? __ldcg(a.pvmax + b) : 0.f;
+            ss[u] = (PN && ok) ? __ldcg(a.psum + b) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             for (int c = 0; c < 2; ++c) {            // static indices: the class arrays stay in registers
                 if (c != cls) continue;
                 if (fbetter(ks[u], ids[u], kb[c], ib[c])) { kb[c] = ks[u]; ib[c] = ids[u]; cb[c] = cs[u]; }
-                if (a.half_p > 0.f) pmerge(a.half_p, pv[c], ps[c], vv[u], ss[u]);
+                if constexpr (PN) pmerge(a.half_p, pv[c], ps[c], vv[u], ss[u]);
             }
         }
     }
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (fbetter(ok, oi, kb[c], ib[c])) { kb[c] = ok; ib[c] = oi; cb[c] = make_float2(ocx, ocy); }
             const float ov = __shfl_xor_sync(0xffffffffu, pv[c], o);
             const float os = __shfl_xor_sync(0xffffffffu, ps[c], o);
-            if (a.half_p > 0.f) pmerge(a.half_p, pv[c], ps[c], ov, os);
+            if constexpr (PN) pmerge(a.half_p, pv[c], ps[c], ov, os);
         }
         if (lane == 0) {
             sk[c][warp] = kb[c]; si[c][warp] = ib[c]; sc2[c][warp] = cb[c];
@@ -233,14 +236,14 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             float v = spv[c][0], sm = sps[c][0];
             for (int w = 1; w < NW; ++w) {
                 if (fbetter(sk[c][w], si[c][w], k, i)) { k = sk[c][w]; i = si[c][w]; x = sc2[c][w]; }
-                if (a.half_p > 0.f) pmerge(a.half_p, v, sm, spv[c][w], sps[c][w]);
+                if constexpr (PN) pmerge(a.half_p, v, sm, spv[c][w], sps[c][w]);
             }
             const float wscale = (a.weight_mode == WM_UNIFORM) ? a.w0 : 1.f;
             const bool any = (k >= 0.f) && (i != 0x7fffffffffffffffLL);
             cell[c] = any ? i : -1;
             chi[c] = x;
             if (!any) cvv[c] = 0.f;
-            else if (a.half_p > 0.f) cvv[c] = wscale * (sqrtf(v) * powf(sm, 0.5f / a.half_p));
+            else if (PN) cvv[c] = wscale * (sqrtf(v) * powf(sm, 0.5f / a.half_p));
             else cvv[c] = wscale * sqrtf(k);
         }
         const int cls = (cvv[0] >= cvv[1]) ? 0 : 1;
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         // winning cell of the exact max and its coefficient g = eps w chi/|chi|
         s_cell[0] = -1;
         s_g = zero2;
-        if (a.half_p <= 0.f && cell_w >= 0) {
+        if (!PN && cell_w >= 0) {
             const long long cc = cell_w;
             int j, d, pair;
             if (cc < 0x7fffffffLL) {
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (n >= N) continue;
             if (need_gx) gx[i] = cadd(cmul(Gm, hm[i]), cmul(g, cmulc(hs[i], ph_x[i])));
             if (need_gh) gh[i] = cadd(cmul(cconj(Gm), xm[i]), cmul(cconj(g), cmul(xq[i], ph_h[i])));
-            if (a.dense_g != nullptr) {
+            if (PN && a.dense_g != nullptr) {
                 const size_t e = (size_t)m * N + n;
                 for (int b = 0; b < a.n_dense; ++b) {
                     const float2* base = a.dense_g + (size_t)b * 2 * M * N;
@@ -500,6 +503,12 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     }  // pass
 }
 
+template <int MODE>
+static cudaError_t launch_mode(const cudaLaunchConfig_t& cfg, const FinArgs& a, bool pn) {
+    return pn ? cudaLaunchKernelEx(&cfg, fin_kernel<1, MODE, true>, a)
+              : cudaLaunchKernelEx(&cfg, fin_kernel<1, MODE, false>, a);
+}
+
 cudaError_t launch_fin(const FinArgs& a_in, cudaStream_t s) {
     FinArgs a = a_in;
     a.eps_f = (float)a.eps;
@@ -530,12 +539,13 @@ cudaError_t launch_fin(const FinArgs& a_in, cudaStream_t s) {
     }
     cfg.attrs = at;
     cfg.numAttrs = na;
+    const bool pn = a.half_p > 0.f;
     switch (a.mode) {
-        case FIN_GRAD_XH: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_GRAD_XH>, a);
-        case FIN_GRAD_U: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_GRAD_U>, a);
-        case FIN_ADAM_H: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_ADAM_H>, a);
-        case FIN_ADAM_U: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_ADAM_U>, a);
-        case FIN_SCORE: return cudaLaunchKernelEx(&cfg, fin_kernel<1, FIN_SCORE>, a);
+        case FIN_GRAD_XH: return launch_mode<FIN_GRAD_XH>(cfg, a, pn);
+        case FIN_GRAD_U: return launch_mode<FIN_GRAD_U>(cfg, a, pn);
+        case FIN_ADAM_H: return launch_mode<FIN_ADAM_H>(cfg, a, pn);
+        case FIN_ADAM_U: return launch_mode<FIN_ADAM_U>(cfg, a, pn);
+        case FIN_SCORE: return launch_mode<FIN_SCORE>(cfg, a, pn);
         default: return cudaErrorInvalidValue;
     }
 }
