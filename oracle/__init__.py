@@ -252,6 +252,61 @@ def sqngd_outer(state, cfg):
     return losses, wpsl
 
 
+# ---------------------------------------------------------------- trainable thresholds
+def loss_grad_u_rho(u, h, rho, a, c, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5,
+                    pnorm=0.0, use_cell=None):
+    """Loss of the soft waveform and its gradient w.r.t. the logits u and the
+    thresholds rho (Eq. 24 with trainable rho_i); returns (terms, gu, grho)."""
+    u = _f64(u)
+    h = _c128(h)
+    rho = _f64(rho)
+    M, N = u.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    terms = np.zeros(6)
+    gu = np.zeros((M, N))
+    gr = np.zeros(rho.size)
+    uc = None if use_cell is None else (ctypes.c_longlong * 1)(int(use_cell))
+    lib().or_loss_grad_u_rho(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                             ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(u),
+                             rho.size, _d(rho), ctypes.c_double(a), ctypes.c_double(c),
+                             _d(h), uc, _d(terms), _d(gu), _d(gr))
+    return terms, gu, gr
+
+
+def project_thresholds(rho):
+    """Nearest ordered set 0 <= rho_0 <= ... <= rho_{K-1} <= 1 (returns a copy)."""
+    r = _f64(rho).copy()
+    lib().or_project_thresholds(r.size, _d(r))
+    return r
+
+
+def sqngd_outer_rho(state, cfg):
+    """One outer iteration of Algorithm 1 with trainable thresholds; state holds
+    float64 u, h, mu, vu, mh, vh, rho, mr, vr and counters t_x, t_h (in place)."""
+    M, N = state["u"].shape
+    nu, w = _grid(cfg["nu"], cfg["k_lo"], cfg["k_hi"], cfg.get("weights"))
+    n_ev = cfg["n_h"] + cfg["n_x"]
+    losses = np.zeros(n_ev)
+    wpsl = np.zeros(n_ev)
+    tx = ctypes.c_longlong(state["t_x"])
+    th = ctypes.c_longlong(state["t_h"])
+    for k in ("rho", "mr", "vr"):
+        assert state[k].dtype == np.float64 and state[k].flags.c_contiguous
+    lib().or_sqngd_outer_rho(
+        M, N, nu.size, _d(nu), cfg["k_lo"], cfg["k_hi"], _d(w), ctypes.c_double(cfg["eps"]),
+        ctypes.c_double(cfg["snrl_db"]), ctypes.c_double(cfg.get("pnorm", 0.0)),
+        cfg["B"], state["rho"].size, _d(state["rho"]), ctypes.c_double(cfg["a"]), ctypes.c_double(cfg["c"]),
+        cfg["n_h"], cfg["n_x"], ctypes.c_double(cfg["lr_h"]), ctypes.c_double(cfg["lr_x"]),
+        ctypes.c_double(cfg["lr_rho"]), ctypes.c_double(cfg.get("b1", 0.9)),
+        ctypes.c_double(cfg.get("b2", 0.999)), ctypes.c_double(cfg.get("adam_eps", 1e-8)),
+        _d(state["u"]), _d(state["h"].view(np.float64)), _d(state["mu"]), _d(state["vu"]),
+        _d(state["mh"].view(np.float64)), _d(state["vh"].view(np.float64)), _d(state["mr"]), _d(state["vr"]),
+        ctypes.byref(tx), ctypes.byref(th), _d(losses), _d(wpsl))
+    state["t_x"] = tx.value
+    state["t_h"] = th.value
+    return losses, wpsl
+
+
 # ---------------------------------------------------------------- SQNAF (h = x)
 def grad_matched(x, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, pnorm=0.0, use_cell=None):
     """Loss L(x, x) and its total gradient when every filter is its waveform

@@ -576,6 +576,118 @@ void or_sqngd_outer(int M, int N, int L, const double* nu, int k_lo, int k_hi,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Trainable thresholds (Section III-C: the rho_i of Eq. 24 "can be treated  */
+/* as trainable parameters"; Algorithm 1 Step B updates them with Adam).     */
+/*   dQ_A/drho_i (z) = -a c (1 - tanh^2(c (z - rho_i)))                      */
+/*   dL/drho_i = sum over elements e of dL/dy_e dQ_A/drho_i (z_e),           */
+/* with dL/dy_e = 2 pi Im(conj(x_e) grad_x e) as in or_loss_grad_u.          */
+/* grho: [K]; the other arguments as in or_loss_grad_u.                      */
+/* ------------------------------------------------------------------------ */
+void or_loss_grad_u_rho(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                        const double* w, double eps, double snrl_db, double pnorm,
+                        const double* u, int K, const double* rho, double a, double c,
+                        const double* h_ri, const long long* use_cell,
+                        double* terms, double* gu, double* grho)
+{
+    int n = M * N;
+    double* x = (double*)malloc(sizeof(double) * 2 * n);
+    double* dy = (double*)malloc(sizeof(double) * n);
+    double* gx = (double*)malloc(sizeof(double) * 2 * n);
+    double* gh = (double*)malloc(sizeof(double) * 2 * n);
+    or_soft_waveform(M, N, u, K, rho, a, c, x, dy);
+    or_grad_xh(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, x, h_ri, use_cell, terms, gx, gh);
+    const cplx* xc = (const cplx*)x;
+    const cplx* gxc = (const cplx*)gx;
+    for (int i = 0; i < K; ++i) grho[i] = 0.0;
+    for (int e = 0; e < n; ++e) {
+        double gy = TWO_PI * cimag(conj(xc[e]) * gxc[e]);
+        double z = 1.0 / (1.0 + exp(-u[e]));
+        if (gu) gu[e] = gy * dy[e] * z * (1.0 - z);
+        for (int i = 0; i < K; ++i) {
+            double t = tanh(c * (z - rho[i]));
+            grho[i] += gy * (-a * c * (1.0 - t * t));
+        }
+    }
+    free(x); free(dy); free(gx); free(gh);
+}
+
+/* Euclidean projection onto the ordered thresholds inside [0, 1]
+ * (Section III-C keeps them "a valid ordered set"; READING: the nearest set
+ * 0 <= rho_0 <= ... <= rho_{K-1} <= 1): isotonic regression by pooling
+ * adjacent violators (Barlow et al. 1972), then clipping to [0, 1] (the
+ * clipped isotonic fit is the projection onto the intersection).  In place. */
+void or_project_thresholds(int K, double* rho)
+{
+    double* val = (double*)malloc(sizeof(double) * K);
+    int* cnt = (int*)malloc(sizeof(int) * K);
+    int nb = 0;
+    for (int i = 0; i < K; ++i) {
+        val[nb] = rho[i];
+        cnt[nb] = 1;
+        ++nb;
+        while (nb > 1 && val[nb - 2] > val[nb - 1]) {   /* pool the violating pair of blocks */
+            double tot = val[nb - 2] * cnt[nb - 2] + val[nb - 1] * cnt[nb - 1];
+            cnt[nb - 2] += cnt[nb - 1];
+            val[nb - 2] = tot / cnt[nb - 2];
+            --nb;
+        }
+    }
+    int i = 0;
+    for (int b = 0; b < nb; ++b) {
+        double v = val[b] < 0.0 ? 0.0 : (val[b] > 1.0 ? 1.0 : val[b]);
+        for (int r = 0; r < cnt[b]; ++r) rho[i++] = v;
+    }
+    free(val); free(cnt);
+}
+
+/* One outer iteration of Algorithm 1 with trainable thresholds: as
+ * or_sqngd_outer, and every Step-B evaluation also takes dL/drho, applies
+ * Adam to rho (same step counter as u, learning rate lr_rho, moments mr, vr)
+ * and projects rho (or_project_thresholds).  rho is updated in place. */
+void or_sqngd_outer_rho(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                        const double* w, double eps, double snrl_db, double pnorm,
+                        int B, int K, double* rho, double a, double c,
+                        int n_h, int n_x, double lr_h, double lr_x, double lr_rho,
+                        double b1, double b2, double adam_eps,
+                        double* u, double* h_ri,
+                        double* mu, double* vu, double* mh, double* vh, double* mr, double* vr,
+                        long long* t_x, long long* t_h,
+                        double* losses_out, double* wpsl_out)
+{
+    int n = M * N;
+    double* xh = (double*)malloc(sizeof(double) * 2 * n);
+    double* gx = (double*)malloc(sizeof(double) * 2 * n);
+    double* gh = (double*)malloc(sizeof(double) * 2 * n);
+    double* gu = (double*)malloc(sizeof(double) * n);
+    double* gr = (double*)malloc(sizeof(double) * K);
+    double terms[6];
+    int it = 0;
+    or_hard_waveform(M, N, u, K, rho, B, NULL, xh);
+    for (int i = 0; i < n_h; ++i) {                       /* Step (A) */
+        or_grad_xh(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, xh, h_ri, NULL,
+                   terms, gx, gh);
+        if (losses_out) losses_out[it] = terms[0];
+        if (wpsl_out) wpsl_out[it] = terms[1];
+        ++it;
+        *t_h += 1;
+        or_adam(2 * n, h_ri, gh, mh, vh, *t_h, lr_h, b1, b2, adam_eps);
+        or_project(M, N, h_ri);
+    }
+    for (int j = 0; j < n_x; ++j) {                       /* Step (B): u and rho */
+        or_loss_grad_u_rho(M, N, L, nu, k_lo, k_hi, w, eps, snrl_db, pnorm, u, K, rho, a, c,
+                           h_ri, NULL, terms, gu, gr);
+        if (losses_out) losses_out[it] = terms[0];
+        if (wpsl_out) wpsl_out[it] = terms[1];
+        ++it;
+        *t_x += 1;
+        or_adam(n, u, gu, mu, vu, *t_x, lr_x, b1, b2, adam_eps);
+        or_adam(K, rho, gr, mr, vr, *t_x, lr_rho, b1, b2, adam_eps);
+        or_project_thresholds(K, rho);
+    }
+    free(xh); free(gx); free(gh); free(gu); free(gr);
+}
+
+/* ------------------------------------------------------------------------ */
 /* SQNAF (Section IV): the delay-Doppler WPSL objective with no receive-     */
 /* filter optimisation -- every filter is the waveform itself, h = x, so     */
 /* the loss is L(x, x) and, by the chain rule through both arguments,        */

@@ -497,3 +497,78 @@ def test_sqnaf_outer_iteration_structure(orc):
     orc.adam(theta, gu, m, v, 1, 1e-2)
     np.testing.assert_array_equal(st["u"], theta)
     assert st["t_x"] == 1
+
+
+# ------------------------------------------------------------------ trainable thresholds
+def test_threshold_gradient_matches_finite_differences(orc):
+    """dL/drho_i through y = Q_A(z; rho) (Eq. 24) against central differences
+    of the loss with rho_i moved, at thresholds inside the elements' windows."""
+    M, N, B, r_n, c = 2, 12, 4, 3, 40.0
+    rho, a = orc.thresholds(B, r_n)
+    u = wl.logits(31, M, N, scale=1.5)
+    h = orc.project(wl.unit_phasors(31, M, N) + 0.2 * wl.complex_normal(31, M, N))
+    kw = dict(nu=wl.full_grid(16), k_lo=-(N - 1), k_hi=N - 1, eps=0.3, snrl_db=0.5)
+    _, gu, gr = orc.loss_grad_u_rho(u, h, rho, a, c, **kw)
+    _, gu2, _ = orc.loss_grad_u(u, h, rho, a, c, **kw)
+    np.testing.assert_allclose(gu, gu2, atol=1e-14)
+    order = np.argsort(-np.abs(gr))
+    assert np.abs(gr[order[0]]) > 1e-3
+    for i in list(order[:6]) + [int(order[-1])]:
+        rp, rm = rho.copy(), rho.copy()
+        rp[i] += 1e-7
+        rm[i] -= 1e-7
+        fd = (orc.loss_grad_u_rho(u, h, rp, a, c, **kw)[0][0] - orc.loss_grad_u_rho(u, h, rm, a, c, **kw)[0][0]) / 2e-7
+        assert abs(fd - gr[i]) <= 1e-5 * max(1.0, abs(gr[i])), (i, fd, gr[i])
+
+
+def test_threshold_projection_is_the_euclidean_projection():
+    """Against a generic constrained least-squares solver on small random sets:
+    the nearest 0 <= rho_0 <= ... <= rho_{K-1} <= 1."""
+    import importlib
+    orc = importlib.import_module("oracle")
+    opt = pytest.importorskip("scipy.optimize")
+    for seed in range(12):
+        K = 3 + seed % 6
+        r = wl.uniform(40 + seed, K, 2) * 1.4 - 0.2          # some outside [0, 1], unordered
+        got = orc.project_thresholds(r)
+        cons = [{"type": "ineq", "fun": (lambda x, i=i: x[i + 1] - x[i])} for i in range(K - 1)]
+        res = opt.minimize(lambda x: np.sum((x - r) ** 2), np.clip(np.sort(r), 0, 1), method="SLSQP",
+                           bounds=[(0.0, 1.0)] * K, constraints=cons, options={"ftol": 1e-14, "maxiter": 500})
+        assert np.all(np.diff(got) >= 0) and got.min() >= 0 and got.max() <= 1
+        assert np.sum((got - r) ** 2) <= res.fun + 1e-9, (seed, got, res.x)
+        np.testing.assert_allclose(got, res.x, atol=1e-5)
+
+
+def test_threshold_projection_keeps_ordered_sets_and_pools_means(orc):
+    rho, _ = orc.thresholds(4, 5)
+    np.testing.assert_array_equal(orc.project_thresholds(rho), rho)
+    r = np.array([0.1, 0.5, 0.3, 0.4, 0.9, 0.8])
+    got = orc.project_thresholds(r)
+    # pooled blocks {0.5, 0.3, 0.4} -> 0.4 and {0.9, 0.8} -> 0.85, means preserved
+    np.testing.assert_allclose(got, [0.1, 0.4, 0.4, 0.4, 0.85, 0.85], atol=1e-15)
+
+
+def test_outer_iteration_with_frozen_thresholds_equals_plain(orc):
+    """lr_rho = 0 leaves rho untouched and reproduces the plain outer iteration;
+    lr_rho > 0 moves rho and keeps it ordered inside [0, 1]."""
+    w = wl.small(2, 16, 4, 16, r_n=5)
+    rho, a = orc.thresholds(w.B, w.r_n)
+    b = wl.phase_indices(3, w.M, w.N, w.B)
+    u = orc.init_logits(b, w.B, w.r_n)
+    h = orc.project(np.exp(2j * np.pi * b / w.B) + 0.1 * wl.complex_normal(3, w.M, w.N))
+    cfg = dict(nu=w.nu, k_lo=w.k_lo, k_hi=w.k_hi, eps=w.eps, snrl_db=w.snrl_db, B=w.B, rho=rho, a=a,
+               c=40.0, n_h=2, n_x=3, lr_h=w.lr_h, lr_x=1e-2, lr_rho=0.0)
+    z = lambda: dict(u=u.copy(), h=h.copy(), mu=np.zeros_like(u), vu=np.zeros_like(u), mh=np.zeros_like(h),
+                     vh=np.zeros_like(h), rho=rho.copy(), mr=np.zeros_like(rho), vr=np.zeros_like(rho),
+                     t_x=0, t_h=0)
+    s1, s2 = z(), z()
+    l1, _ = orc.sqngd_outer_rho(s1, cfg)
+    l2, _ = orc.sqngd_outer(s2, cfg)
+    np.testing.assert_array_equal(l1, l2)
+    np.testing.assert_array_equal(s1["u"], s2["u"])
+    np.testing.assert_array_equal(s1["rho"], rho)
+    cfg["lr_rho"] = 1e-3
+    s3 = z()
+    orc.sqngd_outer_rho(s3, cfg)
+    assert not np.array_equal(s3["rho"], rho)
+    assert np.all(np.diff(s3["rho"]) >= 0) and s3["rho"].min() >= 0 and s3["rho"].max() <= 1
