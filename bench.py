@@ -569,6 +569,11 @@ def _variants(api, wl, dev, stream):
                     "sqngd_evals_per_s": step_rate(c, w, True),
                     "note": "evaluations include the hard-design score of each outer iteration"}
     c.close()
+    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                    n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x, train_rho=True, lr_rho=1e-5)
+    out["trained_thresholds"] = {"workload": w.name + ", the K = 1600 thresholds trained in Step B",
+                                 "sqngd_evals_per_s": step_rate(c, w, False)}
+    c.close()
     return out
 
 

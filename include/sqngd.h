@@ -103,6 +103,11 @@ typedef struct af_config {
                                 receive filter is its waveform, h_m = x_m, so there is no
                                 filter to optimise (needs n_h = 0); losses and gradients
                                 are those of L(x, x) and filter arguments are ignored */
+    int32_t train_rho;       /* 0: thresholds fixed.  1: the rho_i of Eq. 24 are trained in Step B
+                                (Section III-C): Adam on dL/drho with lr_rho after each transmit
+                                step, then the projection of af_project_thresholds.  Needs
+                                K = B r_n <= 8192 */
+    double lr_rho;           /* Adam learning rate of the thresholds, >= 0 */
 } af_config;
 
 /*
@@ -211,6 +216,28 @@ AF_API af_status quantize(af_ctx* ctx, const float* z_dev, int64_t n, int32_t* q
  */
 AF_API af_status soft_quantize(af_ctx* ctx, const float* z_dev, int64_t n, float* y_dev,
                         float* dydz_dev, float* x_dev);
+
+/*
+ * Loss and gradients through the soft transmit chain, as af_loss_grad with
+ * use_hard = 0, plus grad_rho_dev: [K] floats, dL/drho_i of Eq. 24 with the
+ * context's current thresholds (Section III-C):
+ *   sum over elements e of dL/dy_e * (-a c (1 - tanh^2(c (z_e - rho_i)))),
+ * accumulated in a fixed-point sum whose value does not depend on the order
+ * of accumulation.  Needs K <= 8192.  grad_u_dev, grad_h_dev may be NULL.
+ */
+AF_API af_status af_loss_grad_rho(af_ctx* ctx, const float* u_dev, const float* h_dev, double* terms_dev,
+                                  float* grad_u_dev, float* grad_h_dev, float* grad_rho_dev);
+
+/* Copy the context's K thresholds (host [K] floats).  Synchronous. */
+AF_API af_status af_get_thresholds(af_ctx* ctx, float* rho_host);
+
+/*
+ * Projection of K thresholds (device [K] floats, in place) onto the nearest
+ * ordered set 0 <= rho_0 <= ... <= rho_{K-1} <= 1 in the Euclidean sense
+ * (isotonic regression by pooling adjacent violators, then clipping): the
+ * "valid ordered set" of Section III-C.  Needs K <= 8192.
+ */
+AF_API af_status af_project_thresholds(af_ctx* ctx, float* rho_dev);
 
 /* Energy projection of Eq. 32 in place: h_m <- sqrt(N/||h_m||^2) h_m, norms
  * accumulated in FP64.  h_dev complex [M][N]. */

@@ -37,6 +37,7 @@ class AfConfig(ctypes.Structure):
         ("lr_h", c_double), ("lr_x", c_double),
         ("beta1", c_double), ("beta2", c_double), ("adam_eps", c_double),
         ("matched", c_int32),
+        ("train_rho", c_int32), ("lr_rho", c_double),
     ]
 
 
@@ -70,6 +71,9 @@ SIGNATURES = {
     "quantize": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "soft_quantize": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "af_project": (c_int32, [c_void_p, c_void_p]),
+    "af_loss_grad_rho": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "af_get_thresholds": (c_int32, [c_void_p, P_float]),
+    "af_project_thresholds": (c_int32, [c_void_p, c_void_p]),
     "sqngd_init": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sqngd_step": (c_int32, [c_void_p, ctypes.POINTER(AfState), c_int32, P_double]),
     "af_eval_hard": (c_int32, [c_void_p, c_void_p, c_void_p, P_double]),

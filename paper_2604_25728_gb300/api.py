@@ -37,7 +37,8 @@ class Context:
 
     def __init__(self, M, N, B, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, r_n=100,
                  c=300.0, pnorm=0.0, path=AF_PATH_AUTO, n_h=10, n_x=10, lr_h=5e-2, lr_x=5e-4,
-                 beta1=0.9, beta2=0.999, adam_eps=1e-8, matched=False, device=None, stream=None):
+                 beta1=0.9, beta2=0.999, adam_eps=1e-8, matched=False, train_rho=False, lr_rho=1e-5,
+                 device=None, stream=None):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.M, self.N, self.B = int(M), int(N), int(B)
@@ -58,7 +59,8 @@ class Context:
             weights=None if w is None else w.ctypes.data_as(_lib.P_float),
             eps=float(eps), snrl_db=float(snrl_db), r_n=self.r_n, c=self.c, pnorm=float(pnorm),
             path=int(path), n_h=self.n_h, n_x=self.n_x, lr_h=float(lr_h), lr_x=float(lr_x),
-            beta1=float(beta1), beta2=float(beta2), adam_eps=float(adam_eps), matched=int(self.matched))
+            beta1=float(beta1), beta2=float(beta2), adam_eps=float(adam_eps), matched=int(self.matched),
+            train_rho=int(bool(train_rho)), lr_rho=float(lr_rho))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream()
             handle = ctypes.c_void_p()
@@ -132,6 +134,25 @@ class Context:
         self._check(self.lib.af_loss_grad(self.handle, _ptr(u), _ptr(h), int(bool(use_hard)), _ptr(terms),
                                           _ptr(grad_u), _ptr(grad_h)))
         return terms, grad_u, grad_h
+
+    def af_loss_grad_rho(self, u, h, terms=None, grad_u=None, grad_h=None, grad_rho=None):
+        """Loss and gradients through the soft chain, with dL/drho (Eq. 24)."""
+        self._mn(u, "u"); h = self._filters(h)
+        terms = self.empty_terms() if terms is None else terms
+        grad_rho = torch.empty(self.K, dtype=torch.float32, device=self.device) if grad_rho is None else grad_rho
+        self._check(self.lib.af_loss_grad_rho(self.handle, _ptr(u), _ptr(h), _ptr(terms), _ptr(grad_u),
+                                              _ptr(grad_h), _ptr(grad_rho)))
+        return terms, grad_u, grad_h, grad_rho
+
+    def af_get_thresholds(self):
+        r = np.zeros(self.K, dtype=np.float32)
+        self._check(self.lib.af_get_thresholds(self.handle, r.ctypes.data_as(_lib.P_float)))
+        return r
+
+    def af_project_thresholds(self, rho):
+        _need(rho, torch.float32, (self.K,), "rho")
+        self._check(self.lib.af_project_thresholds(self.handle, _ptr(rho)))
+        return rho
 
     def quantize(self, z, q=None, x=None):
         n = z.numel()

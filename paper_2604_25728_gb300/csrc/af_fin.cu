@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (MODE == FIN_ADAM_H) { mh[i] = a.m_h[e]; vh[i] = a.v_h[e]; if (a.snap_best) uu[i] = a.u[e]; }
             if (MODE == FIN_SCORE && a.snap_best) uu[i] = a.u[e];
             if (MODE == FIN_ADAM_U) { uu[i] = a.u[e]; mu[i] = a.m_u[e]; vu[i] = a.v_u[e]; dy[i] = a.dydz[e]; }
-            if (MODE == FIN_GRAD_U && a.grad_u != nullptr) { uu[i] = a.u[e]; dy[i] = a.dydz[e]; }
+            if (MODE == FIN_GRAD_U && (a.grad_u != nullptr || a.gy_out != nullptr)) { uu[i] = a.u[e]; dy[i] = a.dydz[e]; }
         }
     }
     if (!dry) pdl_wait();
@@ -372,11 +372,12 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             if (dry) continue;
             if (a.grad_x) a.grad_x[e] = gx[i];
             if (a.grad_h) a.grad_h[e] = gh[i];
-            if (MODE == FIN_GRAD_U && a.grad_u != nullptr) {
+            if (MODE == FIN_GRAD_U && (a.grad_u != nullptr || a.gy_out != nullptr)) {
                 const float gy = 6.283185307179586f * (xm[i].x * gx[i].y - xm[i].y * gx[i].x);
                 const float z = sigmoidf_(uu[i]);
                 const float gu = gy * dy[i] * z * (1.f - z);
-                a.grad_u[e] = gu;
+                if (a.grad_u) a.grad_u[e] = gu;
+                if (a.gy_out) { a.gy_out[e] = gy; a.z_out[e] = z; }
                 bad |= !isfinite(gu);
             }
         }
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             const float gy = 6.283185307179586f * (xm[i].x * gx[i].y - xm[i].y * gx[i].x);
             const float z = sigmoidf_(uu[i]);
             const float gg = gy * dy[i] * z * (1.f - z);
+            if (!dry && a.gy_out) { a.gy_out[e] = gy; a.z_out[e] = z; }   // for the threshold step
             const float mm_ = a.b1 * mu[i] + (1.f - a.b1) * gg;
             const float vv = a.b2 * vu[i] + (1.f - a.b2) * gg * gg;
             uu[i] -= a.lr * (mm_ / c1) / (sqrtf(vv / c2) + a.adam_eps);

@@ -120,6 +120,10 @@ cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
 struct QuantArgs;
 struct FinArgs;
 struct AccArgs;
+struct RhoArgs;
+int rho_smem_bytes(int K);
+cudaError_t rho_prepare(int K);
+cudaError_t launch_rho(const RhoArgs& a, cudaStream_t s);
 cudaError_t launch_wave_from_logits(const float* u, int n, const QuantArgs& q, int hard, float2* x,
                                     float* dydz, int32_t* qout, cudaStream_t s);
 cudaError_t launch_quantize_z(const float* z, long long n, const QuantArgs& q, int32_t* qout, float2* x,

@@ -29,9 +29,20 @@ namespace af {
 constexpr int kFinThreads = 256;
 
 // ------------------------------------------------------------ wave kernels --
+// A table of thresholds that is not the uniform set (user-set or trained) is
+// staged in shared memory when it fits, so that the binary searches of the
+// quantizers read shared rather than global memory.
+constexpr int kStageK = 8192;
+
 __global__ void wave_from_logits_kernel(const float* __restrict__ u, int n, QuantArgs q, int hard,
                                         float2* __restrict__ x, float* __restrict__ dydz,
                                         int32_t* __restrict__ qout) {
+    extern __shared__ float rho_s[];
+    if (!q.uniform && q.K <= kStageK) {
+        for (int k = threadIdx.x; k < q.K; k += blockDim.x) rho_s[k] = q.rho[k];
+        __syncthreads();
+        q.rho = rho_s;
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float z = sigmoidf_(u[i]);
@@ -166,7 +177,8 @@ __global__ void __launch_bounds__(kFinThreads) acceptance_kernel(const AccArgs a
 // ------------------------------------------------------------ launchers -----
 cudaError_t launch_wave_from_logits(const float* u, int n, const QuantArgs& q, int hard, float2* x,
                                     float* dydz, int32_t* qout, cudaStream_t s) {
-    wave_from_logits_kernel<<<(n + 255) / 256, 256, 0, s>>>(u, n, q, hard, x, dydz, qout);
+    const size_t smem = (!q.uniform && q.K <= kStageK) ? sizeof(float) * q.K : 0;
+    wave_from_logits_kernel<<<(n + 255) / 256, 256, smem, s>>>(u, n, q, hard, x, dydz, qout);
     return cudaGetLastError();
 }
 cudaError_t launch_quantize_z(const float* z, long long n, const QuantArgs& q, int32_t* qout, float2* x,

@@ -85,8 +85,33 @@ struct FinArgs {
     double snrl_db;
     double p_accept2;         // (10^{-(snrl_db + 0.05)/20})^2: a design is acceptable when min p_m^2 >= this
     int matched;              // SQNAF: h = x, the gradient of x is the sum of both partials
+    float* gy_out;            // [M][N] dL/dy and the z it was taken at (trainable thresholds), or null
+    float* z_out;
     // FP32 copies of the double constants above, filled by launch_fin
     float eps_f, ptar_f, inv_N_f, snrl_coef_f, inv_M_f, p_accept2_f;
+};
+
+enum RhoMode : int {
+    RHO_GRAD = 0,      // write dL/drho only
+    RHO_STEP = 1,      // dL/drho, Adam on rho, projection
+    RHO_PROJECT = 2    // projection of rho in place
+};
+
+struct RhoArgs {
+    int mode;                 // RhoMode
+    int n;                    // elements M*N
+    const float* gy;          // [n] dL/dy of the evaluation
+    const float* z;           // [n] z of the evaluation's soft waveform
+    QuantArgs q;              // thresholds (q.rho = the trained table), a, c, window
+    float* rho;               // [K] thresholds, updated in place (RHO_STEP, RHO_PROJECT)
+    long long* acc;           // [K] fixed-point gradient accumulator, left zeroed
+    float* grad_out;          // [K] dL/drho (RHO_GRAD)
+    float* m_rho;             // [K] Adam moments
+    float* v_rho;
+    float lr, b1, b2, adam_eps;
+    const long long* ctr;     // step counters (as FinArgs::ctr)
+    int inner, n_x;           // Step-B index and steps per outer iteration
+    int pdl;
 };
 
 struct AccArgs {

@@ -149,6 +149,11 @@ struct af_ctx {
     long long* pidx64 = nullptr;
     double2* cdiag = nullptr;
     float2* xs = nullptr;      // soft waveform
+    long long* rho_acc = nullptr;  // [K] fixed-point dL/drho accumulator (kept zeroed)
+    float* m_rho = nullptr;    // [K] Adam moments of the trained thresholds
+    float* v_rho = nullptr;
+    float* gy = nullptr;       // [M][N] dL/dy and z of the last transmit evaluation (trained thresholds)
+    float* zb = nullptr;
     float2* xs2 = nullptr;     // second soft buffer (matched mode: x_{j+1} is written while x_j is gathered)
     float* dydz = nullptr;
     float2* xh = nullptr;      // hard waveform
@@ -221,7 +226,7 @@ static QuantArgs quant_args(const af_ctx* c) {
 static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
-                    c->xs, c->xs2, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
+                    c->xs, c->xs2, c->m_rho, c->v_rho, c->rho_acc, c->gy, c->zb, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
                     c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->dense,
                     c->bimg};
     for (void* p : ptrs)
@@ -276,6 +281,9 @@ static af_status validate(const af_config* g, std::string* why) {
         return bad("n_h, n_x must be >= 0 with 1 <= n_h + n_x <= 256");
     if (g->matched != 0 && g->matched != 1) return bad("matched must be 0 or 1");
     if (g->matched && g->n_h != 0) return bad("matched (SQNAF) has no filter step: n_h must be 0");
+    if (g->train_rho != 0 && g->train_rho != 1) return bad("train_rho must be 0 or 1");
+    if (g->train_rho && (long long)g->B * g->r_n > 8192) return bad("train_rho needs K = B r_n <= 8192");
+    if (g->train_rho && !(g->lr_rho >= 0.0 && isfinite(g->lr_rho))) return bad("lr_rho must be finite and >= 0");
     for (int j = 0; j < g->L; ++j)
         if (!isfinite(g->nu[j])) return bad("nu has a non-finite value");
     if (g->weights) {
@@ -461,6 +469,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
                         : dft_prepare_f32(N);
         if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
         if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
+        if (e == cudaSuccess && c->K <= 8192) e = rho_prepare(c->K);
         if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
     }
 
@@ -503,6 +512,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         (s = dalloc(c, &c->pkey64, c->acc_nblk)) || (s = dalloc(c, &c->pidx64, c->acc_nblk)) ||
         (s = dalloc(c, &c->cdiag, M)) || (s = dalloc(c, &c->xs, MN)) || (s = dalloc(c, &c->dydz, MN)) ||
         (cfg->matched && (s = dalloc(c, &c->xs2, MN))) ||
+        (s = dalloc(c, &c->gy, MN)) || (s = dalloc(c, &c->zb, MN)) ||
+        (cfg->train_rho && ((s = dalloc(c, &c->m_rho, c->K)) || (s = dalloc(c, &c->v_rho, c->K)))) ||
+        (c->K <= 8192 && (s = dalloc(c, &c->rho_acc, c->K))) ||
         (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
         (s = dalloc(c, &c->acc_out, 4 + M)) || (s = dalloc(c, &c->terms_scratch, AF_TERMS_FIXED + M)) ||
         (s = dalloc(c, &c->errflag, 1)) || (s = dalloc(c, &c->ctr, 4)) || (s = dalloc(c, &c->best2, 8)))
@@ -510,6 +522,19 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     if (cfg->pnorm > 0.0 &&
         ((s = dalloc(c, &c->adj_part, (size_t)c->nblk * 2 * N)) || (s = dalloc(c, &c->dense, 2 * MN))))
         return fail(s);
+    if (c->rho_acc && cudaMemset(c->rho_acc, 0, sizeof(long long) * c->K) != cudaSuccess) {
+        c->err = "cudaMemset failed";
+        return fail(AF_ERR_CUDA);
+    }
+    if (cfg->train_rho) {
+        // trained thresholds leave the uniform set: every quantizer reads the table
+        c->rho_uniform = false;
+        if (cudaMemset(c->m_rho, 0, sizeof(float) * c->K) != cudaSuccess ||
+            cudaMemset(c->v_rho, 0, sizeof(float) * c->K) != cudaSuccess) {
+            c->err = "cudaMemset failed";
+            return fail(AF_ERR_CUDA);
+        }
+    }
     if (cudaMemset(c->errflag, 0, sizeof(int)) != cudaSuccess) {
         c->err = "cudaMemset failed";
         return fail(AF_ERR_CUDA);
@@ -660,6 +685,24 @@ static FinArgs fin_args(af_ctx* c) {
     return f;
 }
 
+// Arguments of the threshold kernel for this context.
+static RhoArgs rho_args(af_ctx* c, int mode) {
+    RhoArgs r{};
+    r.mode = mode;
+    r.n = c->cfg.M * c->cfg.N;
+    r.gy = c->gy; r.z = c->zb;
+    r.q = quant_args(c);
+    r.rho = c->rho;
+    r.acc = c->rho_acc;
+    r.m_rho = c->m_rho; r.v_rho = c->v_rho;
+    r.lr = (float)c->cfg.lr_rho;
+    r.b1 = (float)c->cfg.beta1; r.b2 = (float)c->cfg.beta2; r.adam_eps = (float)c->cfg.adam_eps;
+    r.ctr = c->ctr;
+    r.n_x = c->cfg.n_x;
+    r.pdl = c->pdl ? 1 : 0;
+    return r;
+}
+
 extern "C" af_status af_ambiguity(af_ctx* c, const float* x, const float* h, float* chi) {
     if (!c) return AF_ERR_INVALID_ARG;
     if (!x || !h || !chi) FAIL(c, AF_ERR_INVALID_ARG, "af_ambiguity: NULL pointer");
@@ -745,6 +788,54 @@ extern "C" af_status af_project(af_ctx* c, float* h) {
     return AF_OK;
 }
 
+extern "C" af_status af_loss_grad_rho(af_ctx* c, const float* u, const float* h, double* terms, float* gu,
+                                      float* gh, float* grho) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (c->K > 8192 || !c->rho_acc) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_rho: needs K <= 8192");
+    if (c->cfg.matched && gh) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_rho: matched context: grad_h must be NULL");
+    if (!u || !grho || (!h && !c->cfg.matched))
+        FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_rho: u, h and grad_rho must not be NULL");
+    const int MN = c->cfg.M * c->cfg.N;
+    if (c->cfg.matched) h = (const float*)c->xs;
+    CK(c, launch_wave_from_logits(u, MN, quant_args(c), 0, c->xs, c->dydz, nullptr, c->stream));
+    CK(c, launch_eval_forward(c, c->xs, (const float2*)h, c->stream, nullptr));
+    FinArgs f = fin_args(c);
+    f.mode = FIN_GRAD_U;
+    f.x = c->xs; f.dydz = c->dydz;
+    f.u = const_cast<float*>(u);
+    f.h_in = (const float2*)h;
+    f.terms = terms;
+    f.grad_u = gu;
+    f.grad_h = (float2*)gh;
+    f.gy_out = c->gy; f.z_out = c->zb;
+    CK(c, launch_fin(f, c->stream));
+    RhoArgs r = rho_args(c, RHO_GRAD);
+    r.grad_out = grho;
+    r.pdl = 0;
+    CK(c, launch_rho(r, c->stream));
+    return AF_OK;
+}
+
+extern "C" af_status af_get_thresholds(af_ctx* c, float* rho_host) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!rho_host) FAIL(c, AF_ERR_INVALID_ARG, "af_get_thresholds: rho is NULL");
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaStreamSynchronize(c->cap));
+    CK(c, cudaMemcpy(rho_host, c->rho, sizeof(float) * c->K, cudaMemcpyDeviceToHost));
+    return AF_OK;
+}
+
+extern "C" af_status af_project_thresholds(af_ctx* c, float* rho) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!rho) FAIL(c, AF_ERR_INVALID_ARG, "af_project_thresholds: rho is NULL");
+    if (c->K > 8192) FAIL(c, AF_ERR_INVALID_ARG, "af_project_thresholds: needs K <= 8192");
+    RhoArgs r = rho_args(c, RHO_PROJECT);
+    r.rho = rho;
+    r.pdl = 0;
+    CK(c, launch_rho(r, c->stream));
+    return AF_OK;
+}
+
 extern "C" af_status sqngd_init(af_ctx* c, const int32_t* b, const float* noise, float* u, float* h) {
     if (!c) return AF_ERR_INVALID_ARG;
     if (!b || !u || !h) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_init: b, u and h must not be NULL");
@@ -803,7 +894,10 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
         f.best2 = c->best2; f.best_q = st->best_q_dev; f.best_h = (float2*)st->best_h_dev;
         f.next_wave = (i == nh - 1) ? NEXT_SOFT : NEXT_NONE;
         f.x_next = c->xs; f.dydz_next = c->dydz;
+        if (c->cfg.train_rho) f.next_wave = NEXT_NONE;      // formed below, thresholds staged
         CK(c, launch_fin(f, s));
+        if (c->cfg.train_rho && i == nh - 1)
+            CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), 0, c->xs, c->dydz, nullptr, s));
     }
     for (int j = 0; j < nx; ++j) {
         // matched: the filters are this evaluation's waveforms, which other rows
@@ -823,7 +917,21 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
         f.next_wave = (j == nx - 1) ? NEXT_HARD : NEXT_SOFT;
         f.x_next = (j == nx - 1) ? c->xh : xn;
         f.dydz_next = c->dydz;
-        CK(c, launch_fin(f, s));
+        if (c->cfg.train_rho) {
+            // Adam on rho needs every element's dL/dy first: the threshold kernels
+            // take the step, then the next waveform is formed with the new rho
+            f.gy_out = c->gy; f.z_out = c->zb;
+            RhoArgs r = rho_args(c, RHO_STEP);
+            r.inner = j;
+            const int next = f.next_wave;
+            f.next_wave = NEXT_NONE;
+            CK(c, launch_fin(f, s));
+            CK(c, launch_rho(r, s));
+            CK(c, launch_wave_from_logits(st->u_dev, MN, quant_args(c), next == NEXT_HARD ? 1 : 0, f.x_next,
+                                          c->dydz, nullptr, s));
+        } else {
+            CK(c, launch_fin(f, s));
+        }
     }
     return AF_OK;
 }
