@@ -574,6 +574,30 @@ def _variants(api, wl, dev, stream):
     out["trained_thresholds"] = {"workload": w.name + ", the K = 1600 thresholds trained in Step B",
                                  "sqngd_evals_per_s": step_rate(c, w, False)}
     c.close()
+    # the transmit-side ResNet generator (Eq. 17) in place of the direct logits
+    P = w.M * w.N
+    b = wl.phase_indices(5, w.M, w.N, w.B)
+    z0 = ((w.r_n // 2) * w.B + b.astype(np.float64)) / (w.B * w.r_n)
+    rn = api.ResNetGenerator(P)
+    th = np.zeros(api.ResNetGenerator.param_count(P), dtype=np.float32)
+    th[-P:] = np.log(z0 / (1 - z0)).ravel()                  # output bias: z = z0 at the start
+    unif = wl.uniform(6, 128 * P, 3)
+    th[:128 * P] = (2 * unif - 1) / np.sqrt(P)               # input layer
+    rn.set_params(th)
+    y0 = torch.from_numpy((b.astype(np.float32) / w.B).ravel()).to(dev)
+    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                    n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=1e-5)
+    u0 = rn.forward(y0).reshape(w.M, w.N).contiguous()
+    _, h0 = c.sqngd_init(torch.from_numpy(b).to(dev))
+    c.attach_generator(rn, y0)
+    st = api.SqngdState.create(u0, h0)
+    c.sqngd_step(st, 2, log=False)
+    dt = timed(lambda: c.sqngd_step(st, 20, log=False), 1)
+    c.af_sync()
+    out["resnet_generator"] = {"workload": w.name + ", the ResNet generator (5 blocks, width 128) trained in Step B",
+                               "sqngd_evals_per_s": 20 * (w.n_h + w.n_x) / dt}
+    c.close()
+    rn.close()
     return out
 
 

@@ -79,6 +79,15 @@ SIGNATURES = {
     "af_eval_hard": (c_int32, [c_void_p, c_void_p, c_void_p, P_double]),
     "af_loss_terms_noalloc": (c_int32, [c_int32, c_int32, c_int32, c_double, c_int32, c_int32, c_double, c_double,
                                         c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rn_param_count": (c_int64, [c_int32]),
+    "rn_create": (c_int32, [c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
+    "rn_destroy": (c_int32, [c_void_p]),
+    "rn_last_error": (ctypes.c_char_p, [c_void_p]),
+    "rn_set_params": (c_int32, [c_void_p, P_float]),
+    "rn_get_params": (c_int32, [c_void_p, P_float]),
+    "rn_forward": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "rn_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
+    "sqngd_attach_generator": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "ws_param_count": (c_int64, []),
     "ws_create": (c_int32, [c_int32, c_int32, c_void_p, ctypes.POINTER(c_void_p)]),
     "ws_destroy": (c_int32, [c_void_p]),

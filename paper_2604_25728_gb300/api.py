@@ -144,6 +144,15 @@ class Context:
                                               _ptr(grad_h), _ptr(grad_rho)))
         return terms, grad_u, grad_h, grad_rho
 
+    def attach_generator(self, rn, y0):
+        """Train the transmit generator rn (ResNetGenerator) in Step B instead of
+        the logits; y0 [M N] float32 on the device; rn = None detaches."""
+        if rn is not None:
+            _need(y0, torch.float32, (self.M * self.N,), "y0")
+        self._generator = (rn, y0)          # keep both alive while attached
+        self._check(self.lib.sqngd_attach_generator(self.handle, None if rn is None else rn.handle,
+                                                    None if rn is None else _ptr(y0)))
+
     def af_get_thresholds(self):
         r = np.zeros(self.K, dtype=np.float32)
         self._check(self.lib.af_get_thresholds(self.handle, r.ctypes.data_as(_lib.P_float)))
@@ -197,6 +206,67 @@ class Context:
         out = np.zeros(4 + self.M, dtype=np.float64)
         self._check(self.lib.af_eval_hard(self.handle, _ptr(u), _ptr(h), out.ctypes.data_as(_lib.P_double)))
         return out
+
+
+class ResNetGenerator:
+    """rn_net: the transmit-side ResNet z = f_theta(y0) of Eq. 17 for P = M N
+    phases (include/resnet.h); forward gives the pre-sigmoid output u."""
+
+    def __init__(self, P: int, device=None, stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.P = int(P)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            handle = ctypes.c_void_p()
+            st = self.lib.rn_create(self.P, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle))
+            self._check(st, None)
+        self.handle = handle
+
+    @staticmethod
+    def param_count(P: int) -> int:
+        return int(_lib.load().rn_param_count(int(P)))
+
+    def _check(self, st, handle):
+        if st != _lib.AF_OK:
+            msg = self.lib.rn_last_error(handle).decode() if handle is not None else ""
+            raise AfError(st, msg)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.param_count(self.P):
+            raise ValueError("wrong parameter count")
+        self._check(self.lib.rn_set_params(self.handle, t.ctypes.data_as(_lib.P_float)), self.handle)
+
+    def get_params(self):
+        t = np.zeros(self.param_count(self.P), dtype=np.float32)
+        self._check(self.lib.rn_get_params(self.handle, t.ctypes.data_as(_lib.P_float)), self.handle)
+        return t
+
+    def forward(self, y0, u=None):
+        _need(y0, torch.float32, (self.P,), "y0")
+        u = torch.empty(self.P, dtype=torch.float32, device=self.device) if u is None else u
+        self._check(self.lib.rn_forward(self.handle, _ptr(y0), _ptr(u)), self.handle)
+        return u
+
+    def train_step(self, y0, du, lr: float, t: int, u=None):
+        _need(y0, torch.float32, (self.P,), "y0")
+        _need(du, torch.float32, (self.P,), "du")
+        u = torch.empty(self.P, dtype=torch.float32, device=self.device) if u is None else u
+        self._check(self.lib.rn_train_step(self.handle, _ptr(y0), _ptr(du), float(lr), int(t), _ptr(u)),
+                    self.handle)
+        return u
 
 
 @dataclass

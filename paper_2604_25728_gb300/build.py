@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsqngd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["sqngd_api.cu", "af_fft.cu", "af_dft.cu", "af_step.cu", "af_fin.cu", "af_adj.cu", "af_noalloc.cu", "af_gemm.cu", "af_ws.cu", "af_rho.cu"]
+SOURCES = ["sqngd_api.cu", "af_fft.cu", "af_dft.cu", "af_step.cu", "af_fin.cu", "af_adj.cu", "af_noalloc.cu", "af_gemm.cu", "af_ws.cu", "af_rho.cu", "af_rn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE]

@@ -467,6 +467,10 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             const float z = sigmoidf_(uu[i]);
             const float gg = gy * dy[i] * z * (1.f - z);
             if (!dry && a.gy_out) { a.gy_out[e] = gy; a.z_out[e] = z; }   // for the threshold step
+            if (a.du_out) {                  // the generator takes the step
+                if (!dry) a.du_out[e] = gg;
+                continue;
+            }
             const float mm_ = a.b1 * mu[i] + (1.f - a.b1) * gg;
             const float vv = a.b2 * vu[i] + (1.f - a.b2) * gg * gg;
             uu[i] -= a.lr * (mm_ / c1) / (sqrtf(vv / c2) + a.adam_eps);

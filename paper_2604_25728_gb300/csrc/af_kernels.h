@@ -121,6 +121,13 @@ struct QuantArgs;
 struct FinArgs;
 struct AccArgs;
 struct RhoArgs;
+}  // namespace af
+struct rn_net;
+namespace af {
+cudaError_t rn_enqueue_step(rn_net* n, const float* y0, const float* du, float* u, const long long* ctr, int inner,
+                            int n_x, float lr, float b1, float b2, float eps, const QuantArgs& q, int next_wave,
+                            float2* x_next, float* dydz_next, int pdl, cudaStream_t s);
+int rn_size(const rn_net* n);
 int rho_smem_bytes(int K);
 cudaError_t rho_prepare(int K);
 cudaError_t launch_rho(const RhoArgs& a, cudaStream_t s);

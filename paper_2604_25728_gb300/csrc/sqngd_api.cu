@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/resnet.h"
 #include "../../include/sqngd.h"
 #include "af_kernels.h"
 #include "af_step.cuh"
@@ -149,6 +150,9 @@ struct af_ctx {
     long long* pidx64 = nullptr;
     double2* cdiag = nullptr;
     float2* xs = nullptr;      // soft waveform
+    rn_net* rn = nullptr;      // attached transmit generator (Eq. 17), or null
+    const float* rn_y0 = nullptr;
+    float* du = nullptr;       // [M][N] dL/du of a transmit evaluation (generator)
     long long* rho_acc = nullptr;  // [K] fixed-point dL/drho accumulator (kept zeroed)
     float* m_rho = nullptr;    // [K] Adam moments of the trained thresholds
     float* v_rho = nullptr;
@@ -226,7 +230,7 @@ static QuantArgs quant_args(const af_ctx* c) {
 static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
-                    c->xs, c->xs2, c->m_rho, c->v_rho, c->rho_acc, c->gy, c->zb, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
+                    c->xs, c->xs2, c->m_rho, c->v_rho, c->rho_acc, c->du, c->gy, c->zb, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
                     c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->dense,
                     c->bimg};
     for (void* p : ptrs)
@@ -512,7 +516,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         (s = dalloc(c, &c->pkey64, c->acc_nblk)) || (s = dalloc(c, &c->pidx64, c->acc_nblk)) ||
         (s = dalloc(c, &c->cdiag, M)) || (s = dalloc(c, &c->xs, MN)) || (s = dalloc(c, &c->dydz, MN)) ||
         (cfg->matched && (s = dalloc(c, &c->xs2, MN))) ||
-        (s = dalloc(c, &c->gy, MN)) || (s = dalloc(c, &c->zb, MN)) ||
+        (s = dalloc(c, &c->gy, MN)) || (s = dalloc(c, &c->zb, MN)) || (s = dalloc(c, &c->du, MN)) ||
         (cfg->train_rho && ((s = dalloc(c, &c->m_rho, c->K)) || (s = dalloc(c, &c->v_rho, c->K)))) ||
         (c->K <= 8192 && (s = dalloc(c, &c->rho_acc, c->K))) ||
         (s = dalloc(c, &c->xh, MN)) || (s = dalloc(c, &c->x64, MN)) || (s = dalloc(c, &c->h64, MN)) ||
@@ -816,6 +820,20 @@ extern "C" af_status af_loss_grad_rho(af_ctx* c, const float* u, const float* h,
     return AF_OK;
 }
 
+extern "C" af_status sqngd_attach_generator(af_ctx* c, rn_net* rn, const float* y0) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (rn && !y0) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_attach_generator: y0 is NULL");
+    if (rn && rn_size(rn) != c->cfg.M * c->cfg.N)
+        FAIL(c, AF_ERR_INVALID_ARG, "sqngd_attach_generator: the generator has %d phases, the context M N = %d",
+             rn_size(rn), c->cfg.M * c->cfg.N);
+    if (rn && c->cfg.train_rho) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_attach_generator: not with trained thresholds");
+    CK(c, cudaStreamSynchronize(c->cap));
+    c->rn = rn;
+    c->rn_y0 = rn ? y0 : nullptr;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }   // the step graph changes
+    return AF_OK;
+}
+
 extern "C" af_status af_get_thresholds(af_ctx* c, float* rho_host) {
     if (!c) return AF_ERR_INVALID_ARG;
     if (!rho_host) FAIL(c, AF_ERR_INVALID_ARG, "af_get_thresholds: rho is NULL");
@@ -917,7 +935,17 @@ static af_status enqueue_outer(af_ctx* c, const af_state* st, cudaStream_t s) {
         f.next_wave = (j == nx - 1) ? NEXT_HARD : NEXT_SOFT;
         f.x_next = (j == nx - 1) ? c->xh : xn;
         f.dydz_next = c->dydz;
-        if (c->cfg.train_rho) {
+        if (c->rn) {
+            // the generator takes the step: dL/du out of the finish kernel, then
+            // Adam on theta, the forward pass to the new u and the next waveform
+            f.du_out = c->du;
+            const int next = f.next_wave;
+            f.next_wave = NEXT_NONE;
+            CK(c, launch_fin(f, s));
+            CK(c, rn_enqueue_step(c->rn, c->rn_y0, c->du, st->u_dev, c->ctr, j, nx, (float)c->cfg.lr_x,
+                                  (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps, quant_args(c),
+                                  next, f.x_next, c->dydz, c->pdl ? 1 : 0, s));
+        } else if (c->cfg.train_rho) {
             // Adam on rho needs every element's dL/dy first: the threshold kernels
             // take the step, then the next waveform is formed with the new rho
             f.gy_out = c->gy; f.z_out = c->zb;

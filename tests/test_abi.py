@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("sqngd.h", "warmstart.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("sqngd.h", "warmstart.h", "resnet.h")]
 
 
 def _declared():
