@@ -578,12 +578,9 @@ def _variants(api, wl, dev, stream):
     P = w.M * w.N
     b = wl.phase_indices(5, w.M, w.N, w.B)
     z0 = ((w.r_n // 2) * w.B + b.astype(np.float64)) / (w.B * w.r_n)
+    from paper_2604_25728_gb300 import generator
     rn = api.ResNetGenerator(P)
-    th = np.zeros(api.ResNetGenerator.param_count(P), dtype=np.float32)
-    th[-P:] = np.log(z0 / (1 - z0)).ravel()                  # output bias: z = z0 at the start
-    unif = wl.uniform(6, 128 * P, 3)
-    th[:128 * P] = (2 * unif - 1) / np.sqrt(P)               # input layer
-    rn.set_params(th)
+    rn.set_params(generator.init_params(P, z0, 5))           # starts at z0, as the direct-logit form
     y0 = torch.from_numpy((b.astype(np.float32) / w.B).ravel()).to(dev)
     c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
                     n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=1e-5)

@@ -81,3 +81,24 @@ def test_adam_matches_torch():
         p.grad = torch.tensor(g, dtype=torch.float64)
         opt.step()
     np.testing.assert_allclose(th, p.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_package_initialisation_starts_at_z0():
+    """The package's generator initialisation (paper_2604_25728_gb300.generator)
+    has the documented layout and, run through the oracle, outputs z0."""
+    pytest.importorskip("torch")
+    from paper_2604_25728_gb300 import _lib
+    try:
+        _lib.load()
+    except Exception:
+        pytest.skip("library not built")
+    from paper_2604_25728_gb300 import generator
+    P = 12
+    z0 = (np.arange(P) + 0.5) / P
+    th = generator.init_params(P, z0, 3).astype(np.float64)
+    assert th.size == rn.param_count(P)
+    parts = rn.unflatten(th, P)
+    assert np.all(parts[-2] == 0) and all(np.all(parts[i] == 0) for i in range(1, len(parts) - 2, 2))
+    assert np.max(np.abs(parts[0])) <= 1 / np.sqrt(P) and np.max(np.abs(parts[2])) <= 1 / np.sqrt(128)
+    u, _ = rn.forward(th, wl.uniform(4, P, 1))
+    np.testing.assert_allclose(1 / (1 + np.exp(-u)), z0, rtol=1e-6)
