@@ -61,8 +61,9 @@ __device__ __forceinline__ int count_lt(const QuantArgs& q, float v) {
 }
 
 // Soft quantizer of Eq. 24 at z.  Thresholds more than `win` below z have
-// tanh = +1 and those more than `win` above have tanh = -1 in FP32, so only
-// the window is evaluated; the saturated ones add 2a each = i0 / B.
+// tanh = +1 and those more than `win` above have tanh = -1 in FP32 (win =
+// 9.5/c: tanh(9.5) rounds to 1), so only the window is evaluated; the
+// saturated ones add 2a each = i0 / B.
 //
 // Uniform thresholds rho_i = (i + 1/2)/K: with e_i = e^{2c(z - rho_i)},
 // tanh(c(z - rho_i)) = 1 - 2/(1 + e_i) and 1 - tanh^2 = 4 e_i/(1 + e_i)^2, and
@@ -71,8 +72,19 @@ __device__ __forceinline__ int count_lt(const QuantArgs& q, float v) {
 // steps), each e_i by one multiply; the terms far from z, where the
 // accumulated rounding of the recursion grows, are saturated.
 __device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, float* dydz, float2* x) {
-    const int i0 = count_lt(q, z - q.win);
-    const int i1 = count_le(q, z + q.win);
+    int i0, i1;
+    if (q.uniform) {
+        // The window's edges need no exact count: a threshold misplaced across
+        // an edge by rounding is saturated there and adds 2a (below) or 0
+        // (above) whichever side counts it, so plain arithmetic does.
+        const float kz = fminf(fmaxf(z, -1.f), 2.f) * (float)q.K;
+        const float kw = q.win * (float)q.K;
+        i0 = min(max((int)ceilf(kz - kw - 0.5f), 0), q.K);
+        i1 = min(max((int)floorf(kz + kw + 0.5f), i0), q.K);
+    } else {
+        i0 = count_lt(q, z - q.win);
+        i1 = count_le(q, z + q.win);
+    }
     float s = 0.f, ds = 0.f;
     if (q.uniform) {
         if (i1 > i0) {

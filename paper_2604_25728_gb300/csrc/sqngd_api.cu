@@ -221,7 +221,7 @@ static QuantArgs quant_args(const af_ctx* c) {
     q.B = c->cfg.B;
     q.a = (float)(1.0 / (2.0 * c->cfg.B));
     q.c = (float)c->cfg.c;
-    q.win = (float)(12.0 / c->cfg.c);
+    q.win = (float)(9.5 / c->cfg.c);     // tanh(9.5) rounds to 1 in FP32
     q.level = c->level;
     q.uniform = c->rho_uniform ? 1 : 0;
     return q;
