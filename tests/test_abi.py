@@ -125,3 +125,31 @@ def test_warmstart_parameter_count_and_host_validation(lib):
         assert lib.ws_create(bad[0], bad[1], None, ctypes.byref(h)) == 1      # AF_ERR_INVALID_ARG
         assert not h.value
     assert lib.ws_destroy(None) == 1
+
+
+def test_generator_host_validation(lib):
+    """rn_* checks that need no device: parameter count, bad sizes, NULLs."""
+    from paper_2604_25728_gb300 import _lib
+    P = 2048
+    assert lib.rn_param_count(P) == 2 * 128 * P + 128 + 5 * (2 * 128 * 128 + 2 * 128) + P
+    assert lib.rn_param_count(0) == -1
+    h = ctypes.c_void_p()
+    assert lib.rn_create(0, None, ctypes.byref(h)) == _lib.AF_ERR_INVALID_ARG and h.value is None
+    assert lib.rn_create(70000, None, ctypes.byref(h)) == _lib.AF_ERR_INVALID_ARG
+    assert lib.rn_create(16, None, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.rn_last_error(None).decode() != ""
+    assert lib.rn_destroy(None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.rn_forward(None, None, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.sqngd_attach_generator(None, None, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.af_loss_grad_rho(None, None, None, None, None, None, None) == _lib.AF_ERR_INVALID_ARG
+    assert lib.af_project_thresholds(None, None) == _lib.AF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bad", [dict(train_rho=2), dict(train_rho=1, B=64, r_n=200), dict(train_rho=1, lr_rho=-1.0),
+                                 dict(train_rho=1, lr_rho=float("nan"))])
+def test_threshold_training_config_rejected_on_host(lib, bad):
+    from paper_2604_25728_gb300 import _lib
+    cfg, nu = _cfg(**bad)
+    h = ctypes.c_void_p()
+    assert lib.af_init(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.AF_ERR_INVALID_ARG
+    assert h.value is None
