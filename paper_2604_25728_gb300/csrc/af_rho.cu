@@ -25,7 +25,8 @@
 namespace af {
 
 constexpr int kRhoThreads = 1024;
-constexpr double kFixScale = 1099511627776.0;   // 2^40
+constexpr float kFixScaleF = 1099511627776.0f;  // 2^40, exact in FP32
+constexpr float kFixInvF = 1.0f / 1099511627776.0f;  // 2^-40, exact
 
 int rho_smem_bytes(int K) { return K * (int)(sizeof(float) + sizeof(long long) + sizeof(int)); }
 static int rho_grad_smem_bytes(int K) { return K * (int)(sizeof(float) + sizeof(long long)); }
@@ -51,8 +52,9 @@ __global__ void __launch_bounds__(kRhoGradThreads) rho_grad_kernel(const RhoArgs
         for (int i = i0; i < i1; ++i) {
             const float t = tanhf(q.c * (z - rs[i]));
             const float g = -gy * ac * (1.f - t * t);
+            // scaling by 2^40 is exact in FP32; the conversion rounds once (no FP64 in the loop)
             atomicAdd(reinterpret_cast<unsigned long long*>(acc + i),
-                      (unsigned long long)__double2ll_rn((double)g * kFixScale));
+                      (unsigned long long)__float2ll_rn(g * kFixScaleF));
         }
     }
     __syncthreads();
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(kRhoThreads) rho_kernel(const RhoArgs a) {
     if (a.mode == RHO_GRAD || a.mode == RHO_STEP) {
         if (a.mode == RHO_GRAD) {
             for (int i = tid; i < K; i += kRhoThreads) {
-                a.grad_out[i] = (float)((double)a.acc[i] / kFixScale);
+                a.grad_out[i] = (float)a.acc[i] * kFixInvF;
                 a.acc[i] = 0;
             }
             return;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kRhoThreads) rho_kernel(const RhoArgs a) {
         __syncthreads();
         const float c1 = s_adam[0], c2 = s_adam[1];
         for (int i = tid; i < K; i += kRhoThreads) {
-            const float g = (float)((double)a.acc[i] / kFixScale);
+            const float g = (float)a.acc[i] * kFixInvF;
             a.acc[i] = 0;
             const float m = a.b1 * a.m_rho[i] + (1.f - a.b1) * g;
             const float v = a.b2 * a.v_rho[i] + (1.f - a.b2) * g * g;
