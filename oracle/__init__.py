@@ -19,8 +19,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "sqngd_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+# SQNGD_ORACLE_SOURCE / SQNGD_ORACLE_BUILD: a test hook that builds the oracle
+# from another copy of the source (tests/test_oracle_mutations.py plants
+# mistakes in such a copy and checks that the pins catch them).
+_SRC = os.environ.get("SQNGD_ORACLE_SOURCE", os.path.join(_HERE, "sqngd_oracle.c"))
+_BUILD = os.environ.get("SQNGD_ORACLE_BUILD", os.path.join(_HERE, "_build"))
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None

@@ -1,0 +1,64 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake
+(a flipped sign or conjugate, a dropped term, a swapped index, a wrong
+constant or comparison) in a scratch copy of oracle/sqngd_oracle.c, builds
+it, and runs the pin suite against it; the suite must fail.  CPU only."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sqngd_oracle.c")
+
+MUTATIONS = [
+    # (name, exact text, replacement)
+    ("phasor sign of Eq. 6", "return cos(TWO_PI * f) + I * sin(TWO_PI * f);",
+     "return cos(TWO_PI * f) - I * sin(TWO_PI * f);"),
+    ("conjugate on the waveform instead of the filter", "s += xm[n] * conj(hl[p]) * phasor",
+     "s += conj(xm[n]) * hl[p] * phasor"),
+    ("auto class keeps tau = 0", "if (m == l) return (k == 0) ? -1 : 0;", "if (m == l) return 0;"),
+    ("SNRL coefficient without (1 - eps)", "cplx G = (1.0 - eps) * (2.0 / M) * (p[m] - ptar)",
+     "cplx G = (2.0 / M) * (p[m] - ptar)"),
+    ("SNRL coefficient at a given cell without (1 - eps)", "cplx G = (1.0 - eps) * (2.0 / M) * (am / N - ptar)",
+     "cplx G = (2.0 / M) * (am / N - ptar)"),
+    ("quantizer scale a = 1/B", "if (a) *a = 1.0 / (2.0 * B);", "if (a) *a = 1.0 / B;"),
+    ("filter gradient without conj(G)", "gh[(size_t)l * N + p] += conj(G) * x[(size_t)m * N + n] * e;",
+     "gh[(size_t)l * N + p] += G * x[(size_t)m * N + n] * e;"),
+    ("chain rule takes Re instead of Im",
+     "double gy = TWO_PI * cimag(conj(xc[e]) * gxc[e]);\n        double z = 1.0 / (1.0 + exp(-u[e]));\n        gu[e] =",
+     "double gy = TWO_PI * creal(conj(xc[e]) * gxc[e]);\n        double z = 1.0 / (1.0 + exp(-u[e]));\n        gu[e] ="),
+    ("threshold chain takes Re instead of Im",
+     "double gy = TWO_PI * cimag(conj(xc[e]) * gxc[e]);\n        double z = 1.0 / (1.0 + exp(-u[e]));\n        if (gu)",
+     "double gy = TWO_PI * creal(conj(xc[e]) * gxc[e]);\n        double z = 1.0 / (1.0 + exp(-u[e]));\n        if (gu)"),
+    ("matched chain takes Re instead of Im", "double gy = TWO_PI * cimag(conj(xc[e]) * gc[e]);",
+     "double gy = TWO_PI * creal(conj(xc[e]) * gc[e]);"),
+    ("hard quantizer counts rho < z", "if (rho[i] <= z[e]) ++cnt;", "if (rho[i] < z[e]) ++cnt;"),
+    ("weight map indexed [L][D]", "return c->w ? c->w[(size_t)d * c->L + j] : 1.0 / (double)c->N;",
+     "return c->w ? c->w[(size_t)j * (c->k_hi - c->k_lo + 1) + d] : 1.0 / (double)c->N;"),
+    ("Adam without bias correction", "double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);",
+     "double c1 = 1.0, c2 = 1.0;"),
+    ("projection scales by N/e", "double s = sqrt((double)N / e);", "double s = (double)N / e;"),
+    ("pooled mean divides by the last block", "val[nb - 2] = tot / cnt[nb - 2];", "val[nb - 2] = tot / cnt[nb - 1];"),
+    ("matched gradient drops the filter partial", "for (int e = 0; e < 2 * n; ++e) g_ri[e] += gh[e];",
+     "for (int e = 0; e < 2 * n; ++e) g_ri[e] += 0.0 * gh[e];"),
+    ("threshold gradient sign", "grho[i] += gy * (-a * c * (1.0 - t * t));", "grho[i] += gy * (a * c * (1.0 - t * t));"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    mutated = tmp_path / "sqngd_oracle.c"
+    mutated.write_text(src.replace(old, new))
+    env = dict(os.environ, SQNGD_ORACLE_SOURCE=str(mutated), SQNGD_ORACLE_BUILD=str(tmp_path / "build"),
+               PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught: {name}\n{r.stdout[-2000:]}"
+    assert "failed" in r.stdout or "error" in r.stdout.lower()

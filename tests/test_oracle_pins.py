@@ -572,3 +572,30 @@ def test_outer_iteration_with_frozen_thresholds_equals_plain(orc):
     orc.sqngd_outer_rho(s3, cfg)
     assert not np.array_equal(s3["rho"], rho)
     assert np.all(np.diff(s3["rho"]) >= 0) and s3["rho"].min() >= 0 and s3["rho"].max() <= 1
+
+
+def test_weighted_classes_by_enumeration(orc):
+    """WAPSL/WCPSL with a non-square [D][L] weight map (D != L), against the
+    pinned ambiguity and the class definitions of Eqs. 8-9 applied by
+    enumeration: every cell of positive weight, auto without tau = 0."""
+    M, N, L = 2, 11, 8
+    k_lo, k_hi = -6, 8
+    D = k_hi - k_lo + 1
+    x, h = _random_pair(41, M, N)
+    nu = 0.013 + np.arange(L) / L
+    w = wl.uniform(42, D * L, 1).reshape(D, L)
+    w[w < 0.2] = 0.0
+    chi = np.abs(orc.ambiguity(x, h, nu, k_lo, k_hi))
+    best = [0.0, 0.0]
+    for m in range(M):
+        for l in range(M):
+            for d in range(D):
+                if m == l and k_lo + d == 0:
+                    continue
+                for j in range(L):
+                    if w[d, j] > 0:
+                        c = 0 if m == l else 1
+                        best[c] = max(best[c], w[d, j] * chi[m, l, d, j])
+    r = orc.loss(x, h, nu, k_lo, k_hi, weights=w, eps=0.4, snrl_db=0.5)
+    assert abs(r["wapsl"] - best[0]) < 1e-12 and abs(r["wcpsl"] - best[1]) < 1e-12
+    assert abs(r["wpsl"] - max(best)) < 1e-12
