@@ -62,3 +62,89 @@ def test_pins_catch_planted_mistake(tmp_path, name, old, new):
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught: {name}\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout or "error" in r.stdout.lower()
+
+
+RN_SRC = os.path.join(ROOT, "oracle", "resnet_oracle.py")
+RN_MUTATIONS = [
+    ("tanh derivative 1 - h", "ds = dh * (1.0 - h * h)", "ds = dh * (1.0 - h)"),
+    ("skip path dropped in the backward pass", "dh = ds + W1.T @ dq", "dh = W1.T @ dq"),
+    ("skip path dropped in the forward pass", "h = np.tanh(h + W2 @ r + b2)", "h = np.tanh(W2 @ r + b2)"),
+    ("first-layer gradient transposed", "g[2 + 4 * k] = np.outer(dq, h_prev)", "g[2 + 4 * k] = np.outer(h_prev, dq)"),
+    ("Adam without bias correction", "theta -= lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)",
+     "theta -= lr * m / (np.sqrt(v) + eps)"),
+    ("output bias not the logit of z0", "parts.append(np.log(z / (1.0 - z)))", "parts.append(np.log(z))"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", RN_MUTATIONS, ids=[m[0] for m in RN_MUTATIONS])
+def test_generator_pins_catch_planted_mistake(tmp_path, name, old, new):
+    """The same for the ResNet generator's oracle: its pins, run against a
+    mutated copy, must fail."""
+    import importlib.util
+
+    import tests.test_resnet_oracle as pins
+    src = open(RN_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    path = tmp_path / "resnet_oracle_mut.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("resnet_oracle_mut", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    saved = pins.rn
+    pins.rn = mod
+    caught = []
+    try:
+        for fn in (pins.test_gradient_matches_finite_differences, pins.test_initial_output_is_z0,
+                   pins.test_zero_blocks_are_identity_through_tanh, pins.test_adam_matches_torch):
+            try:
+                fn()
+            except (AssertionError, pytest.skip.Exception) as e:
+                if isinstance(e, AssertionError):
+                    caught.append(fn.__name__)
+    finally:
+        pins.rn = saved
+    assert caught, f"no pin caught: {name}"
+
+
+WS_SRC = os.path.join(ROOT, "oracle", "warmstart_oracle.py")
+WS_MUTATIONS = [
+    ("convolution tap reversed", "z += W[:, :, t] @ hp[:, t:t + N]", "z += W[:, :, kw - 1 - t] @ hp[:, t:t + N]"),
+    ("softmax gradient without the target", "p[t, np.arange(N)] -= 1.0", "p[t, np.arange(N)] -= 0.0"),
+    ("input gradient with the forward tap order", "gh += W[:, :, t].T @ gp[:, 2 * pad - t:2 * pad - t + N]",
+     "gh += W[:, :, t].T @ gp[:, t:t + N]"),
+    ("tanh derivative 1 - h", "g = gh * (1.0 - hs[li] ** 2)", "g = gh * (1.0 - hs[li])"),
+    ("loss not averaged over elements", "scale = 1.0 / (M * N)", "scale = 1.0 / M"),
+    ("Adam without bias correction", "mh = m_ / (1 - b1 ** t)", "mh = m_"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", WS_MUTATIONS, ids=[m[0] for m in WS_MUTATIONS])
+def test_warmstart_pins_catch_planted_mistake(tmp_path, name, old, new):
+    """The same for the warm-start network's oracle."""
+    import importlib.util
+
+    import tests.test_warmstart_oracle as pins
+    src = open(WS_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
+    path = tmp_path / "warmstart_oracle_mut.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("warmstart_oracle_mut", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    saved = pins.wo
+    pins.wo = mod
+    caught = []
+    try:
+        for nm in dir(pins):
+            fn = getattr(pins, nm)
+            if not (nm.startswith("test_") and callable(fn)):
+                continue
+            try:
+                fn()
+            except AssertionError:
+                caught.append(nm)
+            except pytest.skip.Exception:
+                pass
+    finally:
+        pins.wo = saved
+    assert caught, f"no pin caught: {name}"
