@@ -44,6 +44,20 @@ MUTATIONS = [
     ("matched gradient drops the filter partial", "for (int e = 0; e < 2 * n; ++e) g_ri[e] += gh[e];",
      "for (int e = 0; e < 2 * n; ++e) g_ri[e] += 0.0 * gh[e];"),
     ("threshold gradient sign", "grho[i] += gy * (-a * c * (1.0 - t * t));", "grho[i] += gy * (a * c * (1.0 - t * t));"),
+    ("Eq. 42 weights swapped", "terms[0] = c->eps * lw + (1.0 - c->eps) * ls;",
+     "terms[0] = (1.0 - c->eps) * lw + c->eps * ls;"),
+    ("L_SNRL absolute instead of squared", "ls += (pm - ptar) * (pm - ptar);", "ls += fabs(pm - ptar);"),
+    ("soft-quantizer derivative 1 - t", "ds += a * c * (1.0 - t * t);", "ds += a * c * (1.0 - t);"),
+    ("thresholds i/K", "rho[i] = ((double)i + 0.5) / (double)K;", "rho[i] = (double)i / (double)K;"),
+    ("Adam second moment of g, not g^2", "v[e] = b2 * v[e] + (1.0 - b2) * g[e] * g[e];",
+     "v[e] = b2 * v[e] + (1.0 - b2) * fabs(g[e]);"),
+    ("projection without clipping", "double v = val[b] < 0.0 ? 0.0 : (val[b] > 1.0 ? 1.0 : val[b]);",
+     "double v = val[b];"),
+    ("PSLR normalised by sqrt(N)", "out[0] = 20.0 * log10(psl[0] / (double)N);",
+     "out[0] = 20.0 * log10(psl[0] / sqrt((double)N));"),
+    ("acceptance PSL ignores the weight map", "if (w && !(w[(size_t)d * L + j] > 0)) continue;", ""),
+    ("p-norm without the 1/p root", "if (c->pnorm > 0) return p->vmax * pow(p->psum, 1.0 / c->pnorm);",
+     "if (c->pnorm > 0) return p->vmax * p->psum;"),
 ]
 
 

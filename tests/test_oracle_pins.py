@@ -599,3 +599,33 @@ def test_weighted_classes_by_enumeration(orc):
     r = orc.loss(x, h, nu, k_lo, k_hi, weights=w, eps=0.4, snrl_db=0.5)
     assert abs(r["wapsl"] - best[0]) < 1e-12 and abs(r["wcpsl"] - best[1]) < 1e-12
     assert abs(r["wpsl"] - max(best)) < 1e-12
+
+
+def test_acceptance_metrics_by_enumeration(orc):
+    """Eq. 48 over the ROI (cells of positive weight; auto without tau = 0) and
+    the SNRL of Eq. 10, against the pinned ambiguity by enumeration."""
+    M, N, L = 2, 13, 8
+    k_lo, k_hi = -5, 9
+    D = k_hi - k_lo + 1
+    x, h = _random_pair(43, M, N)
+    h = orc.project(h)
+    nu = 0.021 + np.arange(L) / L
+    w = wl.uniform(44, D * L, 1).reshape(D, L)
+    w[w < 0.35] = 0.0
+    chi = np.abs(orc.ambiguity(x, h, nu, k_lo, k_hi))
+    psl = [0.0, 0.0]
+    for m in range(M):
+        for l in range(M):
+            for d in range(D):
+                if m == l and k_lo + d == 0:
+                    continue
+                for j in range(L):
+                    if w[d, j] > 0:
+                        c = 0 if m == l else 1
+                        psl[c] = max(psl[c], chi[m, l, d, j])
+    out, snrl = orc.metrics(x, h, nu, k_lo, k_hi, weights=w)
+    np.testing.assert_allclose(out[:2], 20 * np.log10(np.array(psl) / N), atol=1e-12)
+    assert abs(out[2] - max(out[0], out[1])) < 1e-12
+    p = np.abs(np.sum(x * np.conj(h), axis=1)) / N
+    np.testing.assert_allclose(snrl, -20 * np.log10(p), atol=1e-12)
+    assert abs(out[3] - np.max(snrl)) < 1e-12
