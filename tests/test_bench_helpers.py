@@ -1,0 +1,50 @@
+"""bench.py's roofline arithmetic and traffic records, on CPU: the algorithmic
+FLOP counts against explicit enumeration of the work each kernel must do."""
+import json
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2604_25728_gb300 import workloads as wl  # noqa: E402
+
+
+def _valid_products(w):
+    return sum(max(0, w.N - abs(k)) for k in range(w.k_lo, w.k_hi + 1))
+
+
+def test_fft_flops_by_enumeration():
+    for w in (wl.tiny(), wl.mid(), wl.small(3, 50, 4, 32, -10, 30)):
+        P, rows = w.M * w.M, w.M * w.M * w.D
+        exp = 6 * P * _valid_products(w) + rows * 5 * w.L * math.log2(w.L) + 3 * rows * w.L
+        assert abs(bench._fwd_flops(w) - exp) < 1e-6 * exp
+    assert abs(bench._fwd_flops(wl.mid()) - 427425792.0) < 1.0
+
+
+def test_split_and_correlation_flops_by_enumeration():
+    w = wl.precision()
+    assert bench._split_flops(w) == 3 * 8 * w.M * w.M * _valid_products(w) * w.L
+    c = wl.correlation()
+    assert _valid_products(c) == c.N * c.N                 # every delay: sum (N - |k|) = N^2
+    assert bench._corr_flops(c) == 8 * 4 * c.N * c.N + 3 * 4 * c.D
+
+
+def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
+    h = bench._source_hash(bench.FWD_SOURCES)
+    assert h == bench._source_hash(bench.FWD_SOURCES) and len(h) == 16
+    rec = {"source_hash": h, "dram_bytes_per_launch": 1234}
+    (tmp_path / "t.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "PROFILES", str(tmp_path))
+    assert bench._traffic_record(h, "t.json") == 1234
+    assert bench._traffic_record("0" * 16, "t.json") is None      # sources changed since the capture
+    assert bench._traffic_record(h, "missing.json") is None
+
+
+def test_committed_traffic_records_name_their_commands():
+    for name in ("fwd_fft_mid_traffic.json", "fwd_gemm_precision_traffic.json"):
+        rec = json.load(open(os.path.join(ROOT, "profiles", name)))
+        assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+        assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
