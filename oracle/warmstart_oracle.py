@@ -6,9 +6,10 @@ imports this module and this module imports nothing from it.
 
 The paper generates the continuous transmit phases with a network f_theta
 whose input is the initial phase configuration y0 (Section II-B, Eq. 17;
-Section IV describes a ResNet).  This build replaces that generator by
-direct logits u optimised by SQNGD plus a small convolutional warm-start
-network that proposes the initial code; the network is not in the paper.
+Section IV describes a ResNet; its oracle is oracle/resnet_oracle.py).  The
+default transmit parameters are direct logits u optimised by SQNGD, with a
+small convolutional warm-start network, not in the paper, proposing the
+initial code.
 What this file computes is therefore its own plain definition:
 
   features F[c][n] (n = 0..N-1, 32 channels):
