@@ -235,7 +235,7 @@ AF_API af_status af_get_thresholds(af_ctx* ctx, float* rho_host);
  * Projection of K thresholds (device [K] floats, in place) onto the nearest
  * ordered set 0 <= rho_0 <= ... <= rho_{K-1} <= 1 in the Euclidean sense
  * (isotonic regression by pooling adjacent violators, then clipping): the
- * "valid ordered set" of Section III-C.  Needs K <= 8192.
+ * ordering that Section III-C requires of the thresholds.  Needs K <= 8192.
  */
 AF_API af_status af_project_thresholds(af_ctx* ctx, float* rho_dev);
 

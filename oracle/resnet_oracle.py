@@ -110,8 +110,8 @@ def adam(theta, g, m, v, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def init_params(P: int, z0, seed_uniform, H: int = WIDTH, blocks: int = BLOCKS):
-    """READING of "Initialize SQN parameters": the hidden layers draw
-    U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from the caller's uniform [0,1)
+    """READING of the initialisation, which Algorithm 1 leaves open: the hidden
+    layers draw U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from the caller's uniform [0,1)
     stream and zero biases; the output layer starts at W_out = 0 and
     b_out = logit(z0), so that z = z0 at the start -- the same initial design
     as the direct-logit form.  seed_uniform(count) -> uniform draws."""

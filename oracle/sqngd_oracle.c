@@ -576,8 +576,8 @@ void or_sqngd_outer(int M, int N, int L, const double* nu, int k_lo, int k_hi,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Trainable thresholds (Section III-C: the rho_i of Eq. 24 "can be treated  */
-/* as trainable parameters"; Algorithm 1 Step B updates them with Adam).     */
+/* Trainable thresholds (Section III-C allows the rho_i of Eq. 24 to be      */
+/* trained; Algorithm 1 Step B updates them with Adam).                      */
 /*   dQ_A/drho_i (z) = -a c (1 - tanh^2(c (z - rho_i)))                      */
 /*   dL/drho_i = sum over elements e of dL/dy_e dQ_A/drho_i (z_e),           */
 /* with dL/dy_e = 2 pi Im(conj(x_e) grad_x e) as in or_loss_grad_u.          */
@@ -612,7 +612,7 @@ void or_loss_grad_u_rho(int M, int N, int L, const double* nu, int k_lo, int k_h
 }
 
 /* Euclidean projection onto the ordered thresholds inside [0, 1]
- * (Section III-C keeps them "a valid ordered set"; READING: the nearest set
+ * (Section III-C requires them ordered; READING: the nearest set
  * 0 <= rho_0 <= ... <= rho_{K-1} <= 1): isotonic regression by pooling
  * adjacent violators (Barlow et al. 1972), then clipping to [0, 1] (the
  * clipped isotonic fit is the projection onto the intersection).  In place. */
