@@ -6,8 +6,14 @@ convergence comparison against the direct-logit form.
 runs SQNGD twice from the same random phases per seed -- once with the
 logits u trained directly (the default transmit parameterisation) and once
 with the ResNet generator producing u from y0 (learning rate 1e-5, Section IV)
--- and prints the final hard PSLR, the max SNRL (FP64, af_eval_hard) and the
-optimiser time of each arm.
+-- and prints the optimiser time of each arm, the hard PSLR and max SNRL (FP64,
+af_eval_hard) of the final design and of the best design that met the SNRL
+target.
+
+    python -m paper_2604_25728_gb300.generator table6
+
+does the same on the optimisation-time settings of the paper's Table VI, one
+JSON line per setting.
 """
 from __future__ import annotations
 
@@ -46,11 +52,11 @@ def init_params(P: int, z0, seed: int) -> np.ndarray:
     return th.astype(np.float32)
 
 
-def _run(w, seed: int, outer: int, generator: bool, lr_net: float):
+def _run(w, seed: int, outer: int, generator: bool, lr_net: float, path: int = api.AF_PATH_AUTO):
     dev = torch.device("cuda", torch.cuda.current_device())
     b = wl.phase_indices(seed, w.M, w.N, w.B)
     ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
-                      n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=lr_net if generator else w.lr_x)
+                      n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=lr_net if generator else w.lr_x, path=path)
     u, h = ctx.sqngd_init(torch.from_numpy(b).to(dev))
     rn = None
     if generator:
@@ -71,11 +77,18 @@ def _run(w, seed: int, outer: int, generator: bool, lr_net: float):
     e1.synchronize()
     ctx.af_sync()
     out = ctx.af_eval_hard(st.u, st.h)
+    res = dict(start_pslr_db=float(start[2]), final_pslr_db=float(out[2]), final_max_snrl_db=float(out[3]),
+               seconds=e0.elapsed_time(e1) / 1e3)
+    best = st.best.cpu().numpy()
+    if best[2] >= 0:
+        # the best hard design whose max SNRL met the target (lowest L_WPSL), re-scored in FP64
+        u_best, _ = ctx.sqngd_init((st.best_q % w.B).to(torch.int32).contiguous())
+        acc = ctx.af_eval_hard(u_best, st.best_h)
+        res.update(best_outer=int(best[2]), best_pslr_db=float(acc[2]), best_max_snrl_db=float(acc[3]))
     ctx.close()
     if rn is not None:
         rn.close()
-    return dict(start_pslr_db=float(start[2]), final_pslr_db=float(out[2]), final_max_snrl_db=float(out[3]),
-                seconds=e0.elapsed_time(e1) / 1e3)
+    return res
 
 
 def compare(which: str = "mid", outer: int = 2000, seeds: int = 3, lr_net: float = 1e-5):
@@ -83,20 +96,46 @@ def compare(which: str = "mid", outer: int = 2000, seeds: int = 3, lr_net: float
     res = {"workload": w.name, "outer_iterations": outer, "lr_generator": lr_net, "lr_logits": w.lr_x}
     for arm, gen in (("direct_logits", False), ("resnet_generator", True)):
         runs = [_run(w, s, outer, gen, lr_net) for s in range(seeds)]
-        res[arm] = {k: float(np.median([r[k] for r in runs])) for k in runs[0]}
+        keys = [k for k in runs[0] if all(k in r for r in runs)]
+        res[arm] = {k: float(np.median([r[k] for r in runs])) for k in keys}
         res[arm]["runs"] = runs
     return res
 
 
+def table6(outer: int = 2000, seed: int = 0, bins: int = 64):
+    """The optimisation-time settings of the paper's Table VI: M in {2, 10},
+    N in {512, 1200}, B in {4, 16}, delays |k| <= 50, Doppler within half a
+    cycle per waveform (|nu| <= 0.5/N cycles per chip; the paper does not give
+    the bin count, `bins` is used), SNRL target 0.5 dB, `outer` iterations of
+    10 + 10 steps, on the split-BF16 tensor-core path (the narrow Doppler
+    window makes the transform a small dense contraction).  Each setting runs
+    with the ResNet generator (the paper's configuration, learning rate 1e-5)
+    and with the direct logits; yields one row per setting with optimiser time
+    and final hard PSLR / max SNRL."""
+    for M in (2, 10):
+        for N in (512, 1200):
+            for B in (4, 16):
+                nu = np.linspace(-0.5 / N, 0.5 / N, bins)
+                w = wl.Workload(f"M={M} N={N} B={B} |k|<=50 {bins} bins on |nu|<=0.5/N", M, N, B, -50, 50, nu)
+                row = {"M": M, "N": N, "B": B, "outer_iterations": outer}
+                for arm, gen in (("resnet_generator", True), ("direct_logits", False)):
+                    row[arm] = _run(w, seed, outer, gen, 1e-5, api.AF_PATH_SPLIT_BF16)
+                yield row
+
+
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("cmd", choices=["compare"])
+    p.add_argument("cmd", choices=["compare", "table6"])
     p.add_argument("--workload", default="mid")
     p.add_argument("--outer", type=int, default=2000)
     p.add_argument("--seeds", type=int, default=3)
     p.add_argument("--lr", type=float, default=1e-5)
     a = p.parse_args()
     t0 = time.time()
+    if a.cmd == "table6":
+        for row in table6(a.outer):
+            print(json.dumps(row), flush=True)
+        return
     r = compare(a.workload, a.outer, a.seeds, a.lr)
     r["wall_seconds"] = time.time() - t0
     print(json.dumps(r))
