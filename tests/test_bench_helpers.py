@@ -48,3 +48,19 @@ def test_committed_traffic_records_name_their_commands():
         rec = json.load(open(os.path.join(ROOT, "profiles", name)))
         assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
         assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+def test_table6_settings_follow_the_paper():
+    """The optimisation-time settings (Table VI): M x N x B over {2, 10} x
+    {512, 1200} x {4, 16}, |k| <= 50, f in [-0.5, 0.5] cycles per waveform
+    (|nu| <= 0.5/N per chip, end points included), SNRL target 0.5 dB, and the
+    Section IV hyper-parameters N_h = N_x = 10, eta_h = 5e-2, eps = 0.1."""
+    from paper_2604_25728_gb300 import generator
+    ws = generator.table6_settings(bins=64)
+    assert sorted((w.M, w.N, w.B) for w in ws) == sorted(
+        (M, N, B) for M in (2, 10) for N in (512, 1200) for B in (4, 16))
+    for w in ws:
+        assert (w.k_lo, w.k_hi, w.L) == (-50, 50, 64)
+        assert abs(w.nu[0] * w.N + 0.5) < 1e-15 and abs(w.nu[-1] * w.N - 0.5) < 1e-15
+        assert all(w.nu[i] < w.nu[i + 1] for i in range(w.L - 1))
+        assert (w.snrl_db, w.n_h, w.n_x, w.lr_h, w.eps) == (0.5, 10, 10, 5e-2, 0.1)
