@@ -185,6 +185,13 @@ def _corr_flops(w) -> float:
     return 8.0 * P * valid + 3.0 * P * w.D
 
 
+def _dump_bytes(w) -> float:
+    """Algorithmic bytes of one materialising forward (af_ambiguity): the
+    complex64 grid [M][M][D][L] written once, plus x and h (complex64 [M][N])
+    read once."""
+    return 8.0 * w.M * w.M * w.D * w.L + 2 * 8.0 * w.M * w.N
+
+
 def _measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -516,9 +523,12 @@ def _tensor_path(api, wl, dev, stream):
 
 
 def _variants(api, wl, dev, stream):
-    """The correlation setting (L = 1, nu = 0: the single-bin correlation
-    kernel) and the SQNAF mode (matched filters) on the mid workload: forward
-    launch time, roofline and optimiser evaluations/s through sqngd_step."""
+    """The materialising forward (af_ambiguity) against the HBM roofline on
+    the mid and differentiation workloads; the correlation setting (L = 1,
+    nu = 0: the single-bin correlation kernel); and, on the mid workload, the
+    SQNAF mode (matched filters), trained thresholds and the ResNet generator:
+    forward launch time, roofline and optimiser evaluations/s through
+    sqngd_step."""
     import torch
 
     e0 = torch.cuda.Event(enable_timing=True)
@@ -546,6 +556,32 @@ def _variants(api, wl, dev, stream):
         return n_outer * evals / dt
 
     out = {}
+    # the materialising forward (af_ambiguity writes chi, complex64 [M][M][D][L]): HBM roofline
+    hbm = _measured_peaks().get("hbm_gbs")
+    mat = {}
+    for name, reps in (("mid", 100), ("differentiation", 10)):
+        w = getattr(wl, name)()
+        try:
+            c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
+            x = torch.from_numpy(wl.unit_phasors(9, w.M, w.N).astype(np.complex64)).to(dev)
+            chi = torch.empty((w.M, w.M, w.D, w.L), dtype=torch.complex64, device=dev)
+            t = timed(lambda: c.af_ambiguity(x, x, chi), reps)
+            nbytes = _dump_bytes(w)
+            gbs = nbytes / t / 1e9
+            mat[name] = {"workload": w.name, "kernel": "fwd_fft_kernel, dump mode (af_ambiguity)",
+                         "launch_us": t * 1e6, "algorithmic_bytes_per_launch": nbytes,
+                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                      "frac": gbs / hbm if hbm else None,
+                                      "peak_source": "measured (hbm_gbs)" if hbm else None,
+                                      "launch_timing": f"{reps} back-to-back af_ambiguity launches between "
+                                                       "two CUDA events"},
+                         "alu_frac": _fwd_flops(w) / t / 1e12 / _fp32_peak_tflops()[0],
+                         "output_vs_l2": "larger than L2" if nbytes > 129e6 else "fits in L2"}
+            del chi
+            c.close()
+        except Exception as e:                     # recorded, so the rest of the line still prints
+            mat[name] = {"error": f"{type(e).__name__}: {e}"}
+    out["materialising_forward"] = mat
     w = wl.correlation()
     c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
                     lr_h=w.lr_h, lr_x=w.lr_x)

@@ -64,3 +64,12 @@ def test_table6_settings_follow_the_paper():
         assert abs(w.nu[0] * w.N + 0.5) < 1e-15 and abs(w.nu[-1] * w.N - 0.5) < 1e-15
         assert all(w.nu[i] < w.nu[i + 1] for i in range(w.L - 1))
         assert (w.snrl_db, w.n_h, w.n_x, w.lr_h, w.eps) == (0.5, 10, 10, 5e-2, 0.1)
+
+
+def test_dump_bytes_by_enumeration():
+    """The materialising forward writes one complex64 per (pair, delay, bin)
+    and reads the complex64 waveforms and filters once."""
+    for w in (wl.tiny(), wl.mid(), wl.small(3, 50, 4, 32, -10, 30)):
+        cells = sum(1 for _m in range(w.M) for _l in range(w.M) for _k in range(w.k_lo, w.k_hi + 1)
+                    for _j in range(w.L))
+        assert bench._dump_bytes(w) == 8 * cells + 8 * 2 * w.M * w.N
