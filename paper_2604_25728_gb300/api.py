@@ -296,6 +296,24 @@ class SqngdState:
                    best_q=torch.zeros(u.shape, dtype=torch.int32, device=u.device), best_h=best_h,
                    best=best)
 
+    _BUFFERS = ("u", "h", "m_u", "v_u", "m_h", "v_h", "best_q", "best_h", "best")
+
+    def save(self, path: str):
+        """Checkpoint every buffer of the state and the step counters to an
+        .npz file.  The context's own state is not included: thresholds set
+        by af_set_thresholds or trained (read them with af_get_thresholds),
+        the thresholds' Adam moments, and an attached generator's parameters
+        (rn_get_params) and moments."""
+        arrays = {k: getattr(self, k).detach().cpu().numpy() for k in self._BUFFERS if getattr(self, k) is not None}
+        np.savez(path, t_h=np.int64(self.t_h), t_x=np.int64(self.t_x), outer=np.int64(self.outer), **arrays)
+
+    @classmethod
+    def load(cls, path: str, device=None):
+        """The state saved by `save`, with its buffers on `device`."""
+        with np.load(path) as f:
+            t = {k: (torch.from_numpy(f[k]).to(device) if k in f.files else None) for k in cls._BUFFERS}
+            return cls(**t, t_h=int(f["t_h"]), t_x=int(f["t_x"]), outer=int(f["outer"]))
+
     def c_struct(self):
         p = lambda t: 0 if t is None else t.data_ptr()
         return _lib.AfState(u_dev=p(self.u), h_dev=p(self.h), m_u_dev=p(self.m_u),
