@@ -45,7 +45,8 @@ AF_API af_status rn_create(int32_t P, void* stream, rn_net** out);
 /* Free the handle (synchronises its stream first). */
 AF_API af_status rn_destroy(rn_net* rn);
 
-/* Message of the last failed call ("" if none); rn may be NULL (rn_create). */
+/* Message of the last failed call ("" if none); rn may be NULL (the calling
+ * thread's last failed rn_create). */
 AF_API const char* rn_last_error(const rn_net* rn);
 
 /* Copy rn_param_count(P) parameters from / to the host and, on set, zero the

@@ -140,7 +140,8 @@ AF_API af_status af_init(const af_config* cfg, void* stream, af_ctx** out);
 AF_API af_status af_destroy(af_ctx* ctx);
 
 /* Message of the last failed call on ctx ("" if none).  ctx may be NULL, in
- * which case the message of the last failed af_init is returned. */
+ * which case the message of the calling thread's last failed af_init is
+ * returned. */
 AF_API const char* af_last_error(const af_ctx* ctx);
 
 /* Path the context resolved to (AF_PATH_FFT, AF_PATH_DFT or AF_PATH_SPLIT_BF16). */

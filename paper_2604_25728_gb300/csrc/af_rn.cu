@@ -431,7 +431,7 @@ struct rn_net {
 };
 
 namespace {
-std::string g_rn_error;
+thread_local std::string g_rn_error;   // failures with no network to hold the message, one per thread
 #define RN_FAIL(n, code, ...)                                         \
     do {                                                              \
         char b_[256];                                                 \

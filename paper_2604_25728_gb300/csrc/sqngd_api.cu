@@ -177,7 +177,8 @@ struct af_ctx {
     size_t g_log_cap = 0;
 };
 
-static std::string g_init_error;
+// messages of failures that have no context to hold them (af_init, af_last_error(NULL)), one per thread
+static thread_local std::string g_init_error;
 
 #define FAIL(ctx, code, ...)                                        \
     do {                                                            \

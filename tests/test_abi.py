@@ -153,3 +153,30 @@ def test_threshold_training_config_rejected_on_host(lib, bad):
     h = ctypes.c_void_p()
     assert lib.af_init(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.AF_ERR_INVALID_ARG
     assert h.value is None
+
+
+def test_context_free_error_messages_are_per_thread(lib):
+    """af_init and rn_create failures have no handle to hold their message:
+    each thread reads the message of its own last failure."""
+    import threading
+    from paper_2604_25728_gb300 import _lib
+    cfg_m, nu_m = _cfg(M=0)
+    cfg_n, nu_n = _cfg(N=1)
+    go = threading.Barrier(2)
+    got = {}
+
+    def worker(name, cfg, P):
+        h = ctypes.c_void_p()
+        assert lib.af_init(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.AF_ERR_INVALID_ARG
+        assert lib.rn_create(P, None, ctypes.byref(h) if P else None) == _lib.AF_ERR_INVALID_ARG
+        go.wait()            # both threads have failed before either reads
+        got[name] = (lib.af_last_error(None).decode(), lib.rn_last_error(None).decode())
+
+    ts = [threading.Thread(target=worker, args=("m", cfg_m, 0)),          # rn_create: NULL out
+          threading.Thread(target=worker, args=("n", cfg_n, 70000))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert "M must be" in got["m"][0] and "N must be" in got["n"][0]
+    assert got["m"][1] == "out is NULL" and got["n"][1] == "P must be in 1..65536"
