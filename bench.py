@@ -1,15 +1,20 @@
 """Throughput of the SQNGD hot path on GB300: AF/CAF loss+grad evaluations/s.
 
-One step = one outer iteration of Algorithm 1 on the mid-size problem (M=4
-waveforms, N=512 chips, B=16 phase levels, every delay |k| <= 511, 512
-Doppler bins over [-0.5, 0.5) cycles/chip): 10 loss+grad evaluations with
-Adam + projection on the filters, then 10 through the soft quantizer with
-Adam on the logits, replayed as one CUDA graph by sqngd_step.  value =
-evaluations per second over all ranks.  Every rank optimises its own seeded
-design (independent problems, no data-path collective; weak scaling).
+One step = one outer iteration of Algorithm 1 on the differentiation-size
+problem (M=4 waveforms, N=2048 chips, B=64 phase levels, every delay
+|k| <= 2047, 2048 Doppler bins over [-0.5, 0.5) cycles/chip), the largest
+workload that runs on one GPU: 10 loss+grad evaluations with Adam and the
+projection on the filters, then 10 through the soft quantizer with Adam on
+the logits, replayed as one CUDA graph by sqngd_step.  value = evaluations
+per second over all ranks.  Every rank optimises its own seeded design
+(independent problems, no data-path collective; weak scaling).
 
---impl reference times the FP64 CPU oracle on the same workload (one
-loss+grad evaluation per step) on the host cores.
+The final JSON line is short (the headline keys plus compact summaries);
+the full record of every leg is printed on the line before it.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a centred delay window of the same problem, scaled to full
+evaluations by its share of the lag products) on the host cores.
 """
 from __future__ import annotations
 
@@ -39,17 +44,21 @@ GEMM_SOURCES = ["paper_2604_25728_gb300/csrc/af_gemm.cu", "paper_2604_25728_gb30
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--legs", default="all", choices=["all", "none"],
+                   help="none: only the headline step, its roofline and e2e (profiler launch lists)")
     p.add_argument("--no-time-to-target", action="store_true",
                    help="skip the time-to-PSL-target experiment (run on rank 0 of a 1-GPU run by default)")
-    p.add_argument("--fwd-path", default="fft", choices=["fft", "split", "corr"],
-                   help="with --fwd-only: fft = the mid workload on the FFT path, split = the narrow-window "
-                        "workload on the tensor-core path, corr = the zero-Doppler correlation setting (L = 1)")
+    p.add_argument("--fwd-path", default="fft", choices=["fft", "fft-mid", "split", "corr", "adj"],
+                   help="with --fwd-only: fft = the differentiation workload on the FFT path, fft-mid = the mid "
+                        "workload, split = the narrow-window workload on the tensor-core path, corr = the "
+                        "zero-Doppler correlation setting (L = 1), adj = whole p-norm evaluations (forward, dense "
+                        "adjoint, finish) on the differentiation workload")
     p.add_argument("--fwd-only", type=int, default=0,
-                   help="run only N launches of the fused forward pass on the workload (for profiler captures)")
+                   help="run only N launches of one kernel's entry point on its workload (profiler captures)")
     return p.parse_args()
 
 
@@ -78,7 +87,7 @@ def max_over_ranks(value: float, device) -> float:
 
 def _workload():
     from paper_2604_25728_gb300 import workloads as wl
-    return wl.mid()
+    return wl.differentiation()
 
 
 def _config(w, extra=None):
@@ -89,6 +98,21 @@ def _config(w, extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+# The oracle's bounded sample: the same problem restricted to the centred
+# delay window |k| <= ORACLE_KW.  Its cost is proportional to its lag products,
+# so one sample evaluation counts as sample_share() of a full evaluation.
+ORACLE_KW = 63
+
+
+def sample_share(w, kw: int = ORACLE_KW) -> float:
+    """Share of the workload's lag products (sum over delays of N - |k|) that
+    the delay window |k| <= kw holds."""
+    ks = np.arange(w.k_lo, w.k_hi + 1)
+    full = np.clip(w.N - np.abs(ks), 0, None).sum()
+    win = np.clip(w.N - np.abs(ks[np.abs(ks) <= kw]), 0, None).sum()
+    return float(win) / float(full)
 
 
 # --------------------------------------------------------------- clocks ----
@@ -160,9 +184,31 @@ def _fwd_flops(w) -> float:
     return 6.0 * P * valid + rows * 5.0 * w.L * np.log2(w.L) + 3.0 * rows * w.L
 
 
-def _fp32_peak_tflops() -> tuple[float, str]:
-    # 152 SMs x 128 FP32 lanes x 2 FLOP/FMA x 2.070 GHz maximum SM clock
-    return 152 * 128 * 2 * 2.070e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+def _fp32_peak_tflops(sms: int | None = None, mhz: float | None = None) -> tuple[float, str]:
+    """FP32 FMA peak from the unit counts: SMs (the device's own count) x 128
+    FP32 lanes x 2 FLOP per FMA x the maximum SM clock (the driver-measured
+    figure when present)."""
+    if sms is None:
+        try:
+            import torch
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        except Exception:
+            sms = None
+    if mhz is None:
+        mhz = _measured_peaks().get("sm_max_mhz")
+    sms = int(sms) if sms else 152
+    mhz = float(mhz) if mhz else 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
+
+
+def _adj_flops(w, rows: int) -> float:
+    """Algorithmic FLOPs of the dense adjoint on `rows` (pair, delay) rows of
+    the winning class: the recomputed forward transform and |chi|^2 (5 L
+    log2 L + 3 L), the coefficient g per cell (3 L: the power and the scale of
+    chi), the transform of conj(g) (5 L log2 L), and per valid lag product the
+    recomputed product (6) and the two gradient accumulations (2 x 8)."""
+    per_row_valid = np.clip(w.N - np.abs(np.arange(w.k_lo, w.k_hi + 1)), 0, None).mean()
+    return rows * (2 * 5.0 * w.L * np.log2(w.L) + 6.0 * w.L + 22.0 * per_row_valid)
 
 
 def _split_flops(w) -> float:
@@ -185,7 +231,16 @@ def _corr_flops(w) -> float:
     return 8.0 * P * valid + 3.0 * P * w.D
 
 
-def paper_fft_wpsl(x, h, nu, k_lo: int, k_hi: int, w: float):
+def paper_fft_phases(nu, N: int, device):
+    """The [L][N] table e^{j 2 pi nu_j n} of the paper's formulation (built in
+    FP64, stored complex64); built once, outside any timed region."""
+    import torch
+    n = torch.arange(N, dtype=torch.float64, device=device)
+    nu_t = torch.as_tensor(np.asarray(nu, dtype=np.float64), device=device)
+    return torch.exp(2j * np.pi * torch.outer(nu_t, n)).to(torch.complex64)
+
+
+def paper_fft_wpsl(x, h, nu, k_lo: int, k_hi: int, w: float, ph=None):
     """Comparison only, never the product path: the forward evaluation as the
     paper formulates it (Section III-D, Eq. 36), Doppler-major through the
     FFT library (torch.fft, FP32; cuFFT on a GPU).  Per waveform and bin one
@@ -193,13 +248,11 @@ def paper_fft_wpsl(x, h, nu, k_lo: int, k_hi: int, w: float):
     per (pair, bin) one inverse FFT of FFT(h_l) conj(FFT(x_m e^{..})), whose
     sample k (mod F) is conj(chi_ml(k, nu_j)).  Returns chi [M][M][D][L] and
     the two maxima of Eqs. 8-9 with the uniform weight w (auto terms skip
-    k = 0)."""
+    k = 0).  ph: the phase table of paper_fft_phases (built here if None)."""
     import torch
     M, N = x.shape
     F = 1 << int(np.ceil(np.log2(2 * N - 1)))
-    n = torch.arange(N, dtype=torch.float64, device=x.device)
-    nu_t = nu if isinstance(nu, torch.Tensor) else torch.as_tensor(np.asarray(nu, dtype=np.float64), device=x.device)
-    ph = torch.exp(2j * np.pi * torch.outer(nu_t, n)).to(torch.complex64)              # [L][N]
+    ph = paper_fft_phases(nu, N, x.device) if ph is None else ph                      # [L][N]
     A = torch.fft.fft(x[:, None, :] * ph[None], n=F)                                   # [M][L][F]
     Hf = torch.fft.fft(h, n=F)                                                         # [M][F]
     c = torch.fft.ifft(Hf[None, :, None, :] * A.conj()[:, None, :, :])                 # [M][M][L][F]
@@ -253,18 +306,28 @@ def _traffic_record(kernel_hash: str, name: str = "fwd_fft_mid_traffic.json"):
 
 
 # --------------------------------------------------------------- oracle ----
-def _oracle_sample(w, seed: int, budget_s: float):
-    """The FP64 oracle on the same workload: loss+grad evaluations (alternating
-    filter and transmit steps) until the time budget is spent."""
+def _oracle_window(w, kw: int = ORACLE_KW):
+    """The oracle's sample problem: w with delays restricted to |k| <= kw."""
+    import dataclasses
+    return dataclasses.replace(w, k_lo=max(w.k_lo, -kw), k_hi=min(w.k_hi, kw))
+
+
+def _oracle_sample(w, seed: int, budget_s: float, kw: int = ORACLE_KW):
+    """The FP64 oracle on a bounded sample of the workload: outer iterations
+    (one filter and one transmit loss+grad evaluation each, with Adam, the
+    projection and the quantizers) on the same problem restricted to the
+    delay window |k| <= kw, until the time budget is spent.  Returns (sample
+    evaluations, seconds, full-evaluation equivalents)."""
     import oracle as orc
     from paper_2604_25728_gb300 import workloads as wl
+    ws = _oracle_window(w, kw)
     rho, a = orc.thresholds(w.B, w.r_n)
     b = wl.phase_indices(seed, w.M, w.N, w.B)
     u = orc.init_logits(b, w.B, w.r_n)
     h = orc.project(np.exp(2j * np.pi * b / w.B))
     st = dict(u=u, h=h, mu=np.zeros_like(u), vu=np.zeros_like(u), mh=np.zeros_like(h), vh=np.zeros_like(h),
               t_x=0, t_h=0)
-    cfg = dict(nu=w.nu, k_lo=w.k_lo, k_hi=w.k_hi, eps=w.eps, snrl_db=w.snrl_db, B=w.B, rho=rho, a=a, c=w.c,
+    cfg = dict(nu=ws.nu, k_lo=ws.k_lo, k_hi=ws.k_hi, eps=w.eps, snrl_db=w.snrl_db, B=w.B, rho=rho, a=a, c=w.c,
                n_h=1, n_x=1, lr_h=w.lr_h, lr_x=w.lr_x)
     evals = 0
     t0 = time.perf_counter()
@@ -274,7 +337,7 @@ def _oracle_sample(w, seed: int, budget_s: float):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return evals, dt
+    return evals, dt, evals * sample_share(w, kw)
 
 
 def _cores() -> int:
@@ -282,6 +345,11 @@ def _cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def _sample_note(w, kw: int = ORACLE_KW) -> str:
+    return (f"the same problem on the delay window |k| <= {kw} ({sample_share(w, kw):.4f} of its lag products); "
+            f"one sample evaluation counts as that share of a full evaluation")
 
 
 # --------------------------------------------------------------- arms ------
@@ -295,24 +363,45 @@ def run_reference(args):
     for _ in range(args.warmup):
         _oracle_sample(w, 0, 0.0)
     t0 = time.perf_counter()
-    evals = 0
+    equiv = 0.0
+    n_samples = 0
     for _ in range(args.steps):
-        e, _ = _oracle_sample(w, 0, 0.0)
-        evals += e
+        e, _, q = _oracle_sample(w, 0, 0.0)
+        equiv += q
+        n_samples += e
     dt = time.perf_counter() - t0
-    v = evals / dt
-    cores = _cores()
+    v = equiv / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": _config(w, {"reference": "FP64 CPU oracle (direct O(M^2 N^2 L) sums, OpenMP), "
-                                                "one filter step + one transmit step per step",
-                                  "l2": "n/a (CPU)"}),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} steps x 2 loss+grad evaluations of the full workload"},
+            "config": _config(w, {"reference": "FP64 CPU oracle (direct O(M^2 N^2 L) sums, OpenMP); each step one "
+                                                "filter and one transmit loss+grad evaluation of the bounded sample",
+                                  "sample": _sample_note(w), "l2": "n/a (CPU)"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                             "sample": f"{args.steps} steps x 2 evaluations of {_sample_note(w)}"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _timer(stream):
+    """fn, reps -> average seconds per call over reps back-to-back calls
+    between two CUDA events on `stream` (after 3 untimed calls)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+    return timed
 
 
 def run_ours(args):
@@ -331,33 +420,16 @@ def run_ours(args):
 
     w = _workload()
     seed = rank_seed(rank)
-    if args.fwd_only > 0 and args.fwd_path in ("split", "corr"):
-        if args.fwd_path == "split":
-            w = wl.precision()
-            ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, path=api.AF_PATH_SPLIT_BF16)
-        else:
-            w = wl.correlation()
-            ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
-        x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
-        for _ in range(args.fwd_only):
-            ctx.af_forward(x, x)
-        ctx.af_sync()
-        ctx.close()
+    if args.fwd_only > 0:
+        _fwd_only(args, api, wl, dev)
         return
     ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
                       n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x)
     stream = torch.cuda.current_stream()
+    timed = _timer(stream)
     b = torch.from_numpy(wl.phase_indices(seed, w.M, w.N, w.B)).to(dev)
     u, h = ctx.sqngd_init(b)
     st = api.SqngdState.create(u, h)
-    if args.fwd_only > 0:
-        xh = torch.empty((w.M, w.N), dtype=torch.complex64, device=dev)
-        ctx.quantize(torch.sigmoid(st.u), x=xh)
-        for _ in range(args.fwd_only):
-            ctx.af_forward(xh, st.h)
-        ctx.af_sync()
-        ctx.close()
-        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     evals_per_step = w.n_h + w.n_x
 
@@ -395,26 +467,15 @@ def run_ours(args):
     value = K * evals_per_step * ws / total_s
 
     # ---- dominant kernel alone: the fused forward pass ------------------------
-    R = 200
+    R = 50
     xh = torch.empty((w.M, w.N), dtype=torch.complex64, device=dev)
     ctx.quantize(torch.sigmoid(st.u), x=xh)
-    fe0 = torch.cuda.Event(enable_timing=True)
-    fe1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(10):
-        ctx.af_forward(xh, st.h)
-    torch.cuda.synchronize()
-    # average launch duration: R back-to-back launches between two events
-    fe0.record(stream)
-    for _ in range(R):
-        ctx.af_forward(xh, st.h)
-    fe1.record(stream)
-    fe1.synchronize()
-    fwd_s = fe0.elapsed_time(fe1) / R / 1e3
+    fwd_s = timed(lambda: ctx.af_forward(xh, st.h), R)
     flops = _fwd_flops(w)
     peak, peak_note = _fp32_peak_tflops()
     achieved = flops / fwd_s / 1e12
     khash = _source_hash(FWD_SOURCES)
-    traffic = _traffic_record(khash)
+    traffic = _traffic_record(khash, "fwd_fft_differentiation_traffic.json")
 
     # ---- end to end through the C ABI with host buffers ------------------------
     pin_u = torch.empty((w.M, w.N), dtype=torch.float32).pin_memory()
@@ -452,58 +513,200 @@ def run_ours(args):
 
     best = st.best.cpu().numpy()
     acc = ctx.af_eval_hard(st.u, st.h)
-    tensor = _tensor_path(api, wl, dev, stream) if rank == 0 else None
-    variants = _variants(api, wl, dev, stream) if rank == 0 else None
+    ctx.close()
+
+    detail = {}
+    if rank == 0 and args.legs == "all":
+        detail["adjoint"] = _guard(lambda: _adjoint_leg(api, wl, dev, timed))
+        detail["mid"] = _guard(lambda: _mid_leg(api, wl, dev, timed))
+        detail["tensor_path"] = _guard(lambda: _tensor_path(api, wl, dev, timed))
+        detail["variants"] = _guard(lambda: _variants(api, wl, dev, timed))
     ttt = None
-    if rank == 0 and ws == 1 and not args.no_time_to_target:
+    if rank == 0 and ws == 1 and not args.no_time_to_target and args.legs == "all":
         from paper_2604_25728_gb300 import warmstart
         try:
             params, rec = warmstart.load()
         except OSError:
             params, rec = None, None
-        ttt = warmstart.time_to_target(params)
-        ttt["warmstart_training"] = None if rec is None else {
-            k: rec[k] for k in ("designs", "outer_iterations", "epochs", "held_out_index_agreement")}
+        ttt = _guard(lambda: warmstart.time_to_target(params))
+        if rec is not None and isinstance(ttt, dict) and "error" not in ttt:
+            ttt["warmstart_training"] = {k: rec[k] for k in rec if k in (
+                "designs", "outer_iterations", "epochs", "held_out_index_agreement")}
+    detail["time_to_target"] = ttt
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        evals, dt = _oracle_sample(w, seed, 12.0)
-        cpu = {"value": evals / dt, "unit": UNIT, "cores": _cores(), "kind": "oracle",
-               "sample": f"{evals} loss+grad evaluations (alternating filter/transmit Adam steps) of the same "
-                         f"workload, {dt:.1f} s of FP64 CPU work"}
+        evals, dt, equiv = _oracle_sample(w, seed, 12.0)
+        cpu = {"value": equiv / dt, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+               "sample": f"{evals} evaluations in {dt:.1f} s of FP64 CPU work on {_sample_note(w)}"}
 
     if rank == 0:
+        roof = {"bound": "alu", "kernel": "fwd_fft_kernel<2048,32> (af_forward)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_note,
+                "algorithmic_flops_per_launch": flops, "launch_us": fwd_s * 1e6,
+                "launch_timing": f"{R} back-to-back af_forward launches between two CUDA events",
+                "traffic": traffic, "kernel_source_hash": khash}
+        detail.update({"roofline": roof, "cpu_baseline": cpu,
+                       "quality": {"best_hard_wpsl_db": float(20 * np.log10(best[0])) if np.isfinite(best[0]) else None,
+                                   "final_pslr_db_fp64": float(acc[2]), "final_max_snrl_db": float(acc[3]),
+                                   "outer_iterations": int(st.outer)}})
+        print(json.dumps({"detail": detail}), flush=True)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(w, {"seed_per_rank": "rank", "path": "FFT (AF_PATH_FFT)"}),
-            "roofline": {"bound": "alu", "kernel": "fwd_fft_kernel<512> (af_forward)", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_note,
-                         "algorithmic_flops_per_launch": flops, "launch_us": fwd_s * 1e6,
-                         "launch_timing": f"{R} back-to-back af_forward launches between two CUDA events",
-                         "traffic": traffic, "kernel_source_hash": khash},
-            "cpu_baseline": cpu,
-            "tensor_path": tensor,
-            "variants": variants,
-            "time_to_target": ttt,
+            "config": {"workload": w.name + ", one outer iteration (20 loss+grad evals) per step",
+                       "path": "FFT", "l2": "flushed between steps (256 MiB memset)"},
+            "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+            "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind")} | {
+                "sample": f"|k|<={ORACLE_KW} window of the workload, scaled by its share of lag products"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # per sqngd_step call: counters, best-record copy in, hard waveform,
             # the graph (forward + finish per evaluation), best-record copy out
             "gpu_launches": K * (2 * evals_per_step + 4),
             "clocks": clocks,
-            "quality": {"best_hard_wpsl_db": float(20 * np.log10(best[0])) if np.isfinite(best[0]) else None,
-                        "final_pslr_db_fp64": float(acc[2]), "final_max_snrl_db": float(acc[3]),
-                        "outer_iterations": int(st.outer)},
+            "more": _summary(detail),
         }
-        print(json.dumps(line), flush=True)
-    ctx.close()
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def _tensor_path(api, wl, dev, stream):
+def _guard(fn):
+    """Run one measurement leg; an exception is recorded in place of its result."""
+    try:
+        return fn()
+    except Exception as e:                          # recorded, so the rest of the line still prints
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
+def _r(v, d=3):
+    return None if v is None else float(f"{v:.{d}g}")
+
+
+def _summary(d: dict) -> dict:
+    """Compact figures of every leg for the final line (3 significant digits)."""
+    out = {}
+    try:
+        a = d.get("adjoint") or {}
+        if "error" not in a:
+            out["adj_pnorm8_us"] = _r(a["adjoint_us"])
+            out["adj_frac"] = _r(a["roofline"]["frac"])
+            out["pnorm8_evals_s"] = _r(a["loss_grad_evals_per_s"])
+        m = d.get("mid") or {}
+        if "error" not in m:
+            out["mid_evals_s"] = _r(m["sqngd_evals_per_s"])
+            out["mid_fwd_frac"] = _r(m["roofline"]["frac"])
+        t = d.get("tensor_path") or {}
+        if "error" not in t:
+            out["split_frac"] = _r(t["roofline"]["frac"])
+            out["split_fwd_us"] = _r(t["split_bf16"]["fwd_launch_us"])
+            out["split_vs_fp32dft"] = _r(t["speedup_fwd_vs_fp32_dft"])
+        v = d.get("variants") or {}
+        mat = (v.get("materialising_forward") or {}).get("differentiation") or {}
+        if "roofline" in mat:
+            out["dump_hbm_frac"] = _r(mat["roofline"]["frac"])
+        pf = v.get("paper_formulation_fft_library") or {}
+        if "fused_speedup" in pf:
+            out["vs_fftlib"] = _r(pf["fused_speedup"])
+        tt = d.get("time_to_target") or {}
+        for arm in ("fp32_random", "split_random", "split_warmstart"):
+            if isinstance(tt.get(arm), dict):
+                out[f"ttt_{arm}_s"] = _r(tt[arm].get("median_s"))
+    except (KeyError, TypeError):
+        pass
+    return out
+
+
+def _fwd_only(args, api, wl, dev):
+    """N launches of one forward kernel on its workload (profiler captures)."""
+    import torch
+    path = args.fwd_path
+    if path == "split":
+        w = wl.precision()
+        ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, path=api.AF_PATH_SPLIT_BF16)
+    elif path == "corr":
+        w = wl.correlation()
+        ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
+    elif path == "adj":
+        w = wl.differentiation()
+        ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, pnorm=8.0)
+    else:
+        w = wl.mid() if path == "fft-mid" else wl.differentiation()
+        ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
+    x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
+    h = torch.from_numpy(wl.unit_phasors(8, w.M, w.N).astype(np.complex64)).to(dev)
+    gx = torch.empty_like(x)
+    gh = torch.empty_like(x)
+    for _ in range(args.fwd_only):
+        if path == "adj":
+            ctx.af_loss_grad_xh(x, h, grad_x=gx, grad_h=gh)
+        else:
+            ctx.af_forward(x, h)
+    ctx.af_sync()
+    ctx.close()
+
+
+def _adjoint_leg(api, wl, dev, timed):
+    """The dense adjoint of the p-norm loss (p = 8) at the differentiation
+    size: the forward pass alone, the whole evaluation (forward, adjoint,
+    partial-row sums, finish) and their difference, the adjoint's share; the
+    spectra are recomputed, never stored."""
+    import torch
+    w = wl.differentiation()
+    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, pnorm=8.0)
+    x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
+    h = torch.from_numpy(wl.unit_phasors(8, w.M, w.N).astype(np.complex64)).to(dev)
+    gx = torch.empty_like(x)
+    gh = torch.empty_like(x)
+    fwd = timed(lambda: c.af_forward(x, h), 20)
+    terms, _, _ = c.af_loss_grad_xh(x, h, grad_x=gx, grad_h=gh)
+    ev = timed(lambda: c.af_loss_grad_xh(x, h, grad_x=gx, grad_h=gh), 20)
+    c.af_sync()
+    cls = int(terms[5].item())
+    c.close()
+    rows = (w.M if cls == 0 else w.M * (w.M - 1)) * w.D
+    adj_s = max(ev - fwd, 1e-9)
+    flops = _adj_flops(w, rows)
+    peak, note = _fp32_peak_tflops()
+    return {"workload": w.name + ", p-norm loss p = 8", "fwd_launch_us": fwd * 1e6,
+            "loss_grad_us": ev * 1e6, "adjoint_us": adj_s * 1e6, "loss_grad_evals_per_s": 1.0 / ev,
+            "winning_class": "auto" if cls == 0 else "cross", "adjoint_rows": rows,
+            "roofline": {"bound": "alu", "achieved": flops / adj_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / adj_s / 1e12 / peak, "peak_source": note,
+                         "algorithmic_flops": flops,
+                         "timing": "adjoint = (forward + adjoint + row sums + finish) - forward, each the average "
+                                   "of 20 back-to-back calls between two CUDA events"}}
+
+
+def _mid_leg(api, wl, dev, timed):
+    """The mid workload (M=4, N=512, 512 bins): optimiser rate through
+    sqngd_step and the forward kernel's ALU roofline."""
+    import torch
+    w = wl.mid()
+    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                    n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x)
+    b = torch.from_numpy(wl.phase_indices(5, w.M, w.N, w.B)).to(dev)
+    u, h = c.sqngd_init(b)
+    st = api.SqngdState.create(u, h)
+    c.sqngd_step(st, 2, log=False)
+    dt = timed(lambda: c.sqngd_step(st, 20, log=False), 3)
+    xh = torch.empty((w.M, w.N), dtype=torch.complex64, device=dev)
+    c.quantize(torch.sigmoid(st.u), x=xh)
+    fwd = timed(lambda: c.af_forward(xh, st.h), 200)
+    c.af_sync()
+    c.close()
+    flops = _fwd_flops(w)
+    peak, note = _fp32_peak_tflops()
+    return {"workload": w.name, "sqngd_evals_per_s": 20 * (w.n_h + w.n_x) / dt, "fwd_launch_us": fwd * 1e6,
+            "roofline": {"bound": "alu", "achieved": flops / fwd / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / fwd / 1e12 / peak, "peak_source": note,
+                         "algorithmic_flops_per_launch": flops,
+                         "traffic": _traffic_record(_source_hash(FWD_SOURCES))}}
+
+
+def _tensor_path(api, wl, dev, timed):
     """The narrow-window workload (M=8, N=1024, |k| <= 255, 64 bins on
     |nu| <= 0.05) on the tcgen05 split-BF16 path, beside the FP32 SIMT DFT
     path: forward launch time, tensor roofline, loss+grad evaluations/s."""
@@ -514,21 +717,6 @@ def _tensor_path(api, wl, dev, stream):
     h = x.clone()
     gx = torch.empty_like(x)
     gh = torch.empty_like(x)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-
-    def timed(fn, reps):
-        """Average duration over `reps` back-to-back calls between two events."""
-        for _ in range(5):
-            fn()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / reps / 1e3
-
     out = {"workload": w.name}
     for name, path, reps in (("split_bf16", api.AF_PATH_SPLIT_BF16, 200), ("fp32_dft", api.AF_PATH_DFT, 40)):
         c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, path=path)
@@ -553,28 +741,15 @@ def _tensor_path(api, wl, dev, stream):
     return out
 
 
-def _variants(api, wl, dev, stream):
+def _variants(api, wl, dev, timed):
     """The materialising forward (af_ambiguity) against the HBM roofline on
-    the mid and differentiation workloads; the correlation setting (L = 1,
-    nu = 0: the single-bin correlation kernel); and, on the mid workload, the
-    SQNAF mode (matched filters), trained thresholds and the ResNet generator:
-    forward launch time, roofline and optimiser evaluations/s through
+    the mid and differentiation workloads; the paper's Doppler-major
+    formulation through the FFT library beside the fused forward; the
+    correlation setting (L = 1, nu = 0: the single-bin correlation kernel);
+    and, on the mid workload, the SQNAF mode (matched filters), trained
+    thresholds and the ResNet generator: optimiser evaluations/s through
     sqngd_step."""
     import torch
-
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-
-    def timed(fn, reps):
-        for _ in range(5):
-            fn()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / reps / 1e3
 
     def step_rate(c, w, matched, n_outer=20):
         b = torch.from_numpy(wl.phase_indices(5, w.M, w.N, w.B)).to(dev)
@@ -591,94 +766,106 @@ def _variants(api, wl, dev, stream):
     hbm = _measured_peaks().get("hbm_gbs")
     mat = {}
     for name, reps in (("mid", 100), ("differentiation", 10)):
-        w = getattr(wl, name)()
-        try:
+        def leg():
+            w = getattr(wl, name)()
             c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
             x = torch.from_numpy(wl.unit_phasors(9, w.M, w.N).astype(np.complex64)).to(dev)
             chi = torch.empty((w.M, w.M, w.D, w.L), dtype=torch.complex64, device=dev)
             t = timed(lambda: c.af_ambiguity(x, x, chi), reps)
             nbytes = _dump_bytes(w)
             gbs = nbytes / t / 1e9
-            mat[name] = {"workload": w.name, "kernel": "fwd_fft_kernel, dump mode (af_ambiguity)",
-                         "launch_us": t * 1e6, "algorithmic_bytes_per_launch": nbytes,
-                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                      "frac": gbs / hbm if hbm else None,
-                                      "peak_source": "measured (hbm_gbs)" if hbm else None,
-                                      "launch_timing": f"{reps} back-to-back af_ambiguity launches between "
-                                                       "two CUDA events"},
-                         "alu_frac": _fwd_flops(w) / t / 1e12 / _fp32_peak_tflops()[0],
-                         "output_vs_l2": "larger than L2" if nbytes > 129e6 else "fits in L2"}
             del chi
             c.close()
-        except Exception as e:                     # recorded, so the rest of the line still prints
-            mat[name] = {"error": f"{type(e).__name__}: {e}"}
+            return {"workload": w.name, "kernel": "fwd_fft_kernel, dump mode (af_ambiguity)",
+                    "launch_us": t * 1e6, "algorithmic_bytes_per_launch": nbytes,
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": gbs / hbm if hbm else None,
+                                 "peak_source": "measured (hbm_gbs)" if hbm else None,
+                                 "launch_timing": f"{reps} back-to-back af_ambiguity launches between two CUDA events"},
+                    "alu_frac": _fwd_flops(w) / t / 1e12 / _fp32_peak_tflops()[0],
+                    "output_vs_l2": "larger than L2" if nbytes > 129e6 else "fits in L2"}
+        mat[name] = _guard(leg)
     out["materialising_forward"] = mat
-    # the paper's own formulation (Eq. 36) through the FFT library, beside the fused kernel
-    try:
+
+    def paper_formulation():
+        # the paper's own formulation (Eq. 36) through the FFT library, beside the fused kernel;
+        # its phase table is built once, outside the timed region, as the library's own tables are
         w = wl.mid()
         c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
         x = torch.from_numpy(wl.unit_phasors(9, w.M, w.N).astype(np.complex64)).to(dev)
         h = torch.from_numpy(wl.unit_phasors(10, w.M, w.N).astype(np.complex64)).to(dev)
-        nu_dev = torch.from_numpy(w.nu).to(dev)           # resident, as the library path's own tables are
-        t_lib = timed(lambda: paper_fft_wpsl(x, h, nu_dev, w.k_lo, w.k_hi, 1.0 / w.N), 10)
+        ph = paper_fft_phases(w.nu, w.N, dev)
+        t_lib = timed(lambda: paper_fft_wpsl(x, h, None, w.k_lo, w.k_hi, 1.0 / w.N, ph=ph), 10)
         t_fused = timed(lambda: c.af_forward(x, h), 100)
         c.close()
-        out["paper_formulation_fft_library"] = {
-            "workload": w.name, "what": "the forward evaluation (chi on the grid and the two sidelobe maxima) in "
-                                        "the paper's Doppler-major FFT formulation through torch.fft (FP32, cuFFT); "
-                                        "comparison only",
-            "ms": t_lib * 1e3, "fused_forward_ms": t_fused * 1e3, "fused_speedup": t_lib / t_fused}
-    except Exception as e:                         # recorded, so the rest of the line still prints
-        out["paper_formulation_fft_library"] = {"error": f"{type(e).__name__}: {e}"}
-    w = wl.correlation()
-    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
-                    lr_h=w.lr_h, lr_x=w.lr_x)
-    x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
-    h = x.clone()
-    fwd = timed(lambda: c.af_forward(x, h), 200)
-    flops = _corr_flops(w)
-    peak, note = _fp32_peak_tflops()
-    out["correlation"] = {
-        "workload": w.name, "kernel": "fwd_corr_kernel (af_forward, L = 1)",
-        "fwd_launch_us": fwd * 1e6, "sqngd_evals_per_s": step_rate(c, w, False),
-        "roofline": {"bound": "alu", "achieved": flops / fwd / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": flops / fwd / 1e12 / peak, "peak_source": note,
-                     "algorithmic_flops_per_launch": flops,
-                     "launch_timing": "200 back-to-back af_forward launches between two CUDA events"}}
-    c.close()
+        return {"workload": w.name, "what": "the forward evaluation (chi on the grid and the two sidelobe maxima) in "
+                                            "the paper's Doppler-major FFT formulation through torch.fft (FP32, "
+                                            "cuFFT); comparison only",
+                "ms": t_lib * 1e3, "fused_forward_ms": t_fused * 1e3, "fused_speedup": t_lib / t_fused}
+    out["paper_formulation_fft_library"] = _guard(paper_formulation)
+
+    def correlation():
+        w = wl.correlation()
+        c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                        lr_h=w.lr_h, lr_x=w.lr_x)
+        x = torch.from_numpy(wl.unit_phasors(7, w.M, w.N).astype(np.complex64)).to(dev)
+        h = x.clone()
+        fwd = timed(lambda: c.af_forward(x, h), 200)
+        flops = _corr_flops(w)
+        peak, note = _fp32_peak_tflops()
+        r = {"workload": w.name, "kernel": "fwd_corr_kernel (af_forward, L = 1)",
+             "fwd_launch_us": fwd * 1e6, "sqngd_evals_per_s": step_rate(c, w, False),
+             "roofline": {"bound": "alu", "achieved": flops / fwd / 1e12, "peak": peak, "unit": "TFLOP/s",
+                          "frac": flops / fwd / 1e12 / peak, "peak_source": note,
+                          "algorithmic_flops_per_launch": flops,
+                          "launch_timing": "200 back-to-back af_forward launches between two CUDA events"}}
+        c.close()
+        return r
+    out["correlation"] = _guard(correlation)
     w = wl.mid()
-    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
-                    n_h=0, n_x=w.n_x, lr_x=w.lr_x, matched=True)
-    out["sqnaf"] = {"workload": w.name + ", matched filters (h = x), no filter step",
-                    "sqngd_evals_per_s": step_rate(c, w, True),
-                    "note": "evaluations include the hard-design score of each outer iteration"}
-    c.close()
-    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
-                    n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x, train_rho=True, lr_rho=1e-5)
-    out["trained_thresholds"] = {"workload": w.name + ", the K = 1600 thresholds trained in Step B",
-                                 "sqngd_evals_per_s": step_rate(c, w, False)}
-    c.close()
-    # the transmit-side ResNet generator (Eq. 17) in place of the direct logits
-    P = w.M * w.N
-    b = wl.phase_indices(5, w.M, w.N, w.B)
-    z0 = ((w.r_n // 2) * w.B + b.astype(np.float64)) / (w.B * w.r_n)
-    from paper_2604_25728_gb300 import generator
-    rn = api.ResNetGenerator(P)
-    rn.set_params(generator.init_params(P, z0, 5))           # starts at z0, as the direct-logit form
-    y0 = torch.from_numpy((b.astype(np.float32) / w.B).ravel()).to(dev)
-    c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
-                    n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=1e-5)
-    u0 = rn.forward(y0).reshape(w.M, w.N).contiguous()
-    _, h0 = c.sqngd_init(torch.from_numpy(b).to(dev))
-    c.attach_generator(rn, y0)
-    st = api.SqngdState.create(u0, h0)
-    c.sqngd_step(st, 2, log=False)
-    dt = timed(lambda: c.sqngd_step(st, 20, log=False), 1)
-    c.af_sync()
-    out["resnet_generator"] = {"workload": w.name + ", the ResNet generator (5 blocks, width 128) trained in Step B",
-                               "sqngd_evals_per_s": 20 * (w.n_h + w.n_x) / dt}
-    c.close()
-    rn.close()
+
+    def sqnaf():
+        c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                        n_h=0, n_x=w.n_x, lr_x=w.lr_x, matched=True)
+        r = {"workload": w.name + ", matched filters (h = x), no filter step",
+             "sqngd_evals_per_s": step_rate(c, w, True),
+             "note": "evaluations include the hard-design score of each outer iteration"}
+        c.close()
+        return r
+    out["sqnaf"] = _guard(sqnaf)
+
+    def trained():
+        c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                        n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=w.lr_x, train_rho=True, lr_rho=1e-5)
+        r = {"workload": w.name + ", the K = 1600 thresholds trained in Step B",
+             "sqngd_evals_per_s": step_rate(c, w, False)}
+        c.close()
+        return r
+    out["trained_thresholds"] = _guard(trained)
+
+    def resnet():
+        # the transmit-side ResNet generator (Eq. 17) in place of the direct logits
+        P = w.M * w.N
+        b = wl.phase_indices(5, w.M, w.N, w.B)
+        z0 = ((w.r_n // 2) * w.B + b.astype(np.float64)) / (w.B * w.r_n)
+        from paper_2604_25728_gb300 import generator
+        rn = api.ResNetGenerator(P)
+        rn.set_params(generator.init_params(P, z0, 5))           # starts at z0, as the direct-logit form
+        y0 = torch.from_numpy((b.astype(np.float32) / w.B).ravel()).to(dev)
+        c = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, eps=w.eps, snrl_db=w.snrl_db, r_n=w.r_n, c=w.c,
+                        n_h=w.n_h, n_x=w.n_x, lr_h=w.lr_h, lr_x=1e-5)
+        u0 = rn.forward(y0).reshape(w.M, w.N).contiguous()
+        _, h0 = c.sqngd_init(torch.from_numpy(b).to(dev))
+        c.attach_generator(rn, y0)
+        st = api.SqngdState.create(u0, h0)
+        c.sqngd_step(st, 2, log=False)
+        dt = timed(lambda: c.sqngd_step(st, 20, log=False), 1)
+        c.af_sync()
+        c.close()
+        rn.close()
+        return {"workload": w.name + ", the ResNet generator (5 blocks, width 128) trained in Step B",
+                "sqngd_evals_per_s": 20 * (w.n_h + w.n_x) / dt}
+    out["resnet_generator"] = _guard(resnet)
     return out
 
 

@@ -54,6 +54,11 @@ AF_API const char* rn_last_error(const rn_net* rn);
 AF_API af_status rn_set_params(rn_net* rn, const float* theta_host);
 AF_API af_status rn_get_params(rn_net* rn, float* theta_host);
 
+/* Copy the Adam moments (rn_param_count(P) floats each) from / to the host,
+ * for checkpoints; set after rn_set_params, which zeroes them.  Synchronous. */
+AF_API af_status rn_set_adam(rn_net* rn, const float* m_host, const float* v_host);
+AF_API af_status rn_get_adam(rn_net* rn, float* m_host, float* v_host);
+
 /* u_dev [P] <- f_theta(y0_dev) before the sigmoid. */
 AF_API af_status rn_forward(rn_net* rn, const float* y0_dev, float* u_dev);
 

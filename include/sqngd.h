@@ -140,8 +140,8 @@ AF_API af_status af_init(const af_config* cfg, void* stream, af_ctx** out);
 AF_API af_status af_destroy(af_ctx* ctx);
 
 /* Message of the last failed call on ctx ("" if none).  ctx may be NULL, in
- * which case the message of the calling thread's last failed af_init is
- * returned. */
+ * which case the message of the calling thread's last failed call that has
+ * no context (af_init, af_loss_terms_noalloc) is returned. */
 AF_API const char* af_last_error(const af_ctx* ctx);
 
 /* Path the context resolved to (AF_PATH_FFT, AF_PATH_DFT or AF_PATH_SPLIT_BF16). */
@@ -186,6 +186,8 @@ AF_API af_status af_forward(af_ctx* ctx, const float* x_dev, const float* h_dev)
  * Matched contexts (cfg.matched = 1): h_dev is ignored (may be NULL), the
  * loss is L(x, x), grad_x_dev receives its total gradient (the sum of the
  * transmit and filter partials at h = x) and grad_h_dev must be NULL.
+ * With both gradient outputs NULL the p-norm loss skips its dense adjoint
+ * (the loss terms alone are computed).
  */
 AF_API af_status af_loss_grad_xh(af_ctx* ctx, const float* x_dev, const float* h_dev,
                           double* terms_dev, float* grad_x_dev, float* grad_h_dev);
@@ -196,7 +198,8 @@ AF_API af_status af_loss_grad_xh(af_ctx* ctx, const float* x_dev, const float* h
  * use_hard = 0; the hard waveform of Eq. 43 (no gradient to u) when
  * use_hard = 1.  u_dev: [M][N]; h_dev complex [M][N];
  * grad_u_dev: [M][N] (ignored when use_hard = 1), grad_h_dev complex [M][N];
- * terms_dev as in af_loss_grad_xh.  Any output may be NULL.
+ * terms_dev as in af_loss_grad_xh.  Any output may be NULL; with no
+ * gradient output the p-norm loss skips its dense adjoint.
  * Matched contexts: h_dev is ignored (may be NULL), grad_u_dev is the
  * gradient of L(x, x) and grad_h_dev must be NULL.
  */
@@ -257,7 +260,12 @@ AF_API af_status sqngd_init(af_ctx* ctx, const int32_t* b_dev, const float* nois
 /*
  * n_outer outer iterations of Algorithm 1: X_hard from u; n_h x {loss and
  * grad_H at X_hard; Adam on (H_Re, H_Im); projection (Eq. 32)}; n_x x {X_soft
- * from u; loss and grad_u; Adam on u}.  One outer iteration is replayed as a
+ * from u; loss and grad_u; Adam on u}.  Precision inside the step: the
+ * products and transforms in FP32; A_mm(0,0) and the projection norms
+ * ||h_m||^2 as double-float sums of exact FP32 products (about 44
+ * significant bits); p_m, L_SNRL, the SNRL gradient coefficient and the
+ * loss assembly in FP64; the projection's scale factor in FP32 (below the
+ * FP32 rounding of the stored taps).  One outer iteration is replayed as a
  * CUDA graph.  The first evaluation of every outer iteration scores the
  * current hard design; the best one (lowest L_WPSL among designs whose max
  * SNRL is within 0.05 dB of the target) is copied to best_q/best_h.
@@ -271,6 +279,48 @@ AF_API af_status sqngd_init(af_ctx* ctx, const int32_t* b_dev, const float* nois
  * the log has 1 + n_x evaluations per outer iteration (the score first).
  */
 AF_API af_status sqngd_step(af_ctx* ctx, af_state* st, int32_t n_outer, double* log_host);
+
+/* Record of the stopping rule, kept by the caller between calls (and in
+ * checkpoints) so that a resumed run applies the rule as an uninterrupted one. */
+typedef struct af_stop {
+    double best_wpsl;        /* lowest hard L_WPSL scored so far; +inf before the first */
+    int64_t best_outer;      /* outer iteration (st->outer numbering) that scored it; a negative
+                                value (a fresh record) is set to st->outer - 1 by sqngd_run */
+    int32_t stopped;         /* out: 0 not stopped, 1 the patience rule fired, 2 t_max reached */
+} af_stop;
+
+/*
+ * Algorithm 1 with its stopping test (Section III-C): training ends when
+ * further outer iterations bring no improvement in the WPSL, or when the
+ * maximum number T of outer iterations is reached.  Reading: the WPSL is
+ * the hard design's L_WPSL, scored by the first evaluation of every outer
+ * iteration (the Step-A evaluation at X_hard, or the hard-design score of a
+ * matched context); an outer iteration improves when that value is strictly
+ * below stop->best_wpsl; the run stops after outer iteration t as soon as
+ * t - stop->best_outer >= patience, or once st->outer reaches t_max.
+ * The iterations run through sqngd_step in chunks sized so that the rule can
+ * fire only at a chunk's last iteration, so the stop is exact (no iteration
+ * beyond it runs) and the results equal those of sqngd_step over the same
+ * number of iterations.  Each chunk's log is read back (synchronous call).
+ * log_host: NULL, or room for [t_max - st->outer][evals][4] doubles as in
+ * sqngd_step, of which the first *n_done rows are written.  patience >= 1.
+ * Needs a hard evaluation in every outer iteration: n_h >= 1, or matched.
+ */
+AF_API af_status sqngd_run(af_ctx* ctx, af_state* st, int64_t t_max, int32_t patience, af_stop* stop,
+                           double* log_host, int64_t* n_done);
+
+/*
+ * The quantization thresholds' state, for checkpoints: rho [K], their Adam
+ * moments m_rho, v_rho [K] (zero unless cfg.train_rho), and `uniform`: 1 when
+ * the quantizers use the default set rho_i = (i + 1/2)/K computed by
+ * arithmetic, 0 when they read the table (user-set or trained thresholds).
+ * Host buffers; m_host, v_host may be NULL.  Synchronous.  The setter
+ * accepts any non-decreasing rho in [0, 1]; uniform = 1 requires rho to be
+ * the default set.
+ */
+AF_API af_status af_get_rho_state(af_ctx* ctx, float* rho_host, float* m_host, float* v_host, int32_t* uniform);
+AF_API af_status af_set_rho_state(af_ctx* ctx, const float* rho_host, const float* m_host, const float* v_host,
+                                  int32_t uniform);
 
 /*
  * Acceptance metrics in FP64 on the GPU (Eq. 48 and Eq. 10) for the hard
@@ -305,7 +355,8 @@ AF_API af_status af_eval_hard(af_ctx* ctx, const float* u_dev, const float* h_de
  * make it before any stream capture.  Calls share the array, so calls that
  * overlap on the GPU race; every call rewrites the scratch it reads, so
  * nothing needs clearing between calls.  Returns AF_ERR_CUDA if a lookup or
- * launch fails.
+ * launch fails.  On any failure af_last_error(NULL), called from the same
+ * thread, gives the reason.
  */
 AF_API af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, double nu0, int32_t k_lo, int32_t k_hi,
                                        double eps, double snrl_db, const float* x_dev, const float* h_dev,

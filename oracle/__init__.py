@@ -98,6 +98,32 @@ def ambiguity_cells(x, h, nu, k_lo, k_hi, cells):
     return out
 
 
+def fd_losses(x, h, nu, k_lo, k_hi, coords, weights=None, eps=0.1, snrl_db=0.5, pnorm=0.0):
+    """Losses (Eq. 42) with one sample replaced, for central finite
+    differences on grids too large to re-evaluate per coordinate: coords is a
+    list of (target, row, col, v_plus, v_minus) with target 0 for x[row, col]
+    and 1 for h[row, col]; returns (loss_plus, loss_minus) arrays.  chi is
+    updated by the rank-one change of each replacement (Eq. 6 is linear in
+    x_m(n) and in conj(h_l(p))); only the pairs of that row or column move."""
+    x, h = _c128(x), _c128(h)
+    M, N = x.shape
+    nu, w = _grid(nu, k_lo, k_hi, weights)
+    n = len(coords)
+    tgt = np.ascontiguousarray([int(c[0]) for c in coords], dtype=np.int32)
+    row = np.ascontiguousarray([int(c[1]) for c in coords], dtype=np.int32)
+    col = np.ascontiguousarray([int(c[2]) for c in coords], dtype=np.int32)
+    vp = _c128([complex(c[3]) for c in coords])
+    vm = _c128([complex(c[4]) for c in coords])
+    assert np.all((tgt == 0) | (tgt == 1)) and np.all((row >= 0) & (row < M)) and np.all((col >= 0) & (col < N))
+    lp = np.zeros(n)
+    lm = np.zeros(n)
+    lib().or_fd_losses(M, N, nu.size, _d(nu), k_lo, k_hi, _d(w), ctypes.c_double(eps),
+                       ctypes.c_double(snrl_db), ctypes.c_double(pnorm), _d(x), _d(h), n,
+                       tgt.ctypes.data_as(_ip), row.ctypes.data_as(_ip), col.ctypes.data_as(_ip),
+                       _d(vp), _d(vm), _d(lp), _d(lm))
+    return lp, lm
+
+
 # ---------------------------------------------------------------- loss, Eqs. 7-9, 37-42
 def loss(x, h, nu, k_lo, k_hi, weights=None, eps=0.1, snrl_db=0.5, pnorm=0.0):
     """Returns dict(loss, wpsl, wapsl, wcpsl, snrl_term, cls, p[M], cells[2])."""
@@ -361,6 +387,29 @@ def sqnaf_outer(state, cfg):
         _d(state["u"]), _d(state["mu"]), _d(state["vu"]), ctypes.byref(tx), _d(losses), _d(wpsl))
     state["t_x"] = tx.value
     return losses, wpsl
+
+
+def stop_rule(wpsl, patience, t_max, best_wpsl=float("inf"), best_outer=-1, t0=0):
+    """Algorithm 1's stopping test (Section III-C): training ends when further
+    outer iterations bring no improvement in the WPSL, or after T outer
+    iterations.  Read as: wpsl[i] is the hard design's L_WPSL scored by outer
+    iteration t0 + i; an iteration improves when its value is strictly below
+    the best so far; the run stops after iteration t once t - (iteration of
+    the best) >= patience (a fresh record counts from t0 - 1), or at t_max.
+    Returns (iterations run, 1 patience / 2 t_max / 0 the sequence ran out,
+    best value, its iteration)."""
+    if best_outer < 0:
+        best_outer = t0 - 1
+    t = t0
+    for v in wpsl:
+        if t >= t_max:
+            return t - t0, 2, best_wpsl, best_outer
+        if v < best_wpsl:
+            best_wpsl, best_outer = v, t
+        if t - best_outer >= patience:
+            return t + 1 - t0, 1, best_wpsl, best_outer
+        t += 1
+    return t - t0, (2 if t >= t_max else 0), best_wpsl, best_outer
 
 
 def metrics(x, h, nu, k_lo, k_hi, weights=None):

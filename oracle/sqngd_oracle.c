@@ -42,6 +42,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -338,23 +341,56 @@ void or_grad_xh(int M, int N, int L, const double* nu, int k_lo, int k_hi,
             if (mag > 0) add_cell_grad(&c, x, h, cell, eps * cell_weight(&c, d, j) * a / mag, gx, gh);
         }
     } else if (pk[cls].any && pk[cls].vmax > 0) {
-        /* d/dv_c (sum v^p)^(1/p) = (v_c / V)^(p-1), V the class p-norm */
+        /* d/dv_c (sum v^p)^(1/p) = (v_c / V)^(p-1), V the class p-norm.  Every
+         * cell of the winning class adds G = eps w (w|chi|/V)^(p-1) chi/|chi|
+         * through the two adjoint sums above (as add_cell_grad, with the
+         * phasors from a table).  Rows are split over threads with private
+         * accumulators, summed in thread order afterwards. */
         double V = class_value(&c, &pk[cls]);
         long long rows = (long long)M * M * D;
-        for (long long r = 0; r < rows; ++r) {
-            int d = (int)(r % D), pair = (int)(r / D), m = pair / M, l = pair % M;
-            int k = k_lo + d;
-            if (cell_class(m, l, k) != cls) continue;
-            for (int j = 0; j < L; ++j) {
-                double wt = cell_weight(&c, d, j);
-                if (wt <= 0) continue;
-                cplx a = af_cell(N, x + (size_t)m * N, h + (size_t)l * N, k, nu[j]);
-                double mag = cabs(a);
-                if (mag <= 0) continue;
-                double coef = eps * pow(wt * mag / V, pnorm - 1.0) * wt;
-                add_cell_grad(&c, x, h, r * L + j, coef * a / mag, gx, gh);
+        cplx* E = phasor_table(N, L, nu);
+        int nt = 1;
+#ifdef _OPENMP
+        nt = omp_get_max_threads();
+#endif
+        cplx* acc = (cplx*)calloc((size_t)nt * 2 * M * N, sizeof(cplx));
+#pragma omp parallel num_threads(nt)
+        {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            cplx* tgx = acc + (size_t)tid * 2 * M * N;
+            cplx* tgh = tgx + (size_t)M * N;
+#pragma omp for schedule(static)
+            for (long long r = 0; r < rows; ++r) {
+                int d = (int)(r % D), pair = (int)(r / D), m = pair / M, l = pair % M;
+                int k = k_lo + d;
+                if (cell_class(m, l, k) != cls) continue;
+                for (int j = 0; j < L; ++j) {
+                    double wt = cell_weight(&c, d, j);
+                    if (wt <= 0) continue;
+                    const cplx* e = E + (size_t)j * N;
+                    cplx a = af_cell_tab(N, x + (size_t)m * N, h + (size_t)l * N, k, e);
+                    double mag = cabs(a);
+                    if (mag <= 0) continue;
+                    cplx G = eps * pow(wt * mag / V, pnorm - 1.0) * wt * a / mag;
+                    for (int n = 0; n < N; ++n) {
+                        int q = n + k;
+                        if (q < 0 || q >= N) continue;
+                        tgx[(size_t)m * N + n] += G * h[(size_t)l * N + q] * conj(e[n]);
+                        tgh[(size_t)l * N + q] += conj(G) * x[(size_t)m * N + n] * e[n];
+                    }
+                }
             }
         }
+        for (int t = 0; t < nt; ++t)
+            for (size_t i = 0; i < (size_t)M * N; ++i) {
+                gx[i] += acc[(size_t)t * 2 * M * N + i];
+                gh[i] += acc[(size_t)t * 2 * M * N + (size_t)M * N + i];
+            }
+        free(acc);
+        free(E);
     }
     /* SNRL term: L_SNRL = (1/M) sum (p_m - p_tar)^2, p_m = |A_mm(0,0)|/N with
      * A_mm(0,0) = sum_n x_m(n) conj(h_m(n)) (Eq. 38, nu = 0, tau = 0). */
@@ -855,4 +891,204 @@ void or_grad_at_cell(int M, int N, int L, const double* nu, int k_lo, int k_hi,
             gh[(size_t)m * N + n] += conj(G) * x[(size_t)m * N + n];
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Losses at perturbed inputs, for central finite differences at full size. */
+/* Coordinate c replaces one sample -- x_row(col) when target[c] = 0,        */
+/* h_row(col) when target[c] = 1 -- by vp[c] (the + side) and by vm[c] (the  */
+/* - side).  Eq. 6 is linear in x_m(n) and in conj(h_l(p)), so              */
+/*   x_m(n) -> x_m(n) + delta  moves chi_ml(k, nu) by                        */
+/*                delta conj(h_l(n+k)) e^{j 2 pi nu n}         (all l, k, nu) */
+/*   h_l(p) -> h_l(p) + delta  moves chi_ml(k, nu) by                        */
+/*                x_m(p-k) conj(delta) e^{j 2 pi nu (p-k)}     (all m, k, nu) */
+/* a rank-one change that touches only the M pairs of one row (or column)   */
+/* of the pair grid.  Every other pair keeps the class peak (and p-norm sum) */
+/* of the unperturbed grid, so each perturbed loss costs one pass over M     */
+/* pairs' cells instead of a full evaluation.  The SNRL term (Eqs. 38, 41)   */
+/* is recomputed from the perturbed inputs, and the loss assembled as in     */
+/* or_loss (Eqs. 7-9, 37, 42).  The test suite checks this routine against   */
+/* or_loss on explicitly perturbed inputs.                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double vmax;   /* max of w|chi| over the pair's cells of its class */
+    double psum;   /* sum of (w|chi| / vmax)^p over them (p-norm only) */
+    int any;
+} fd_stat;
+
+/* Fold (v, s) into a running (vmax, psum): both sums rescaled to the larger max. */
+static void fd_fold(double pnorm, fd_stat* a, double v, double s)
+{
+    if (!a->any) { a->vmax = v; a->psum = s; a->any = 1; return; }
+    if (pnorm <= 0) { if (v > a->vmax) a->vmax = v; return; }
+    if (v > a->vmax) {
+        a->psum = (a->vmax > 0 ? a->psum * pow(a->vmax / v, pnorm) : 0.0) + s;
+        a->vmax = v;
+    } else {
+        a->psum += (v > 0 ? s * pow(v / a->vmax, pnorm) : 0.0);
+    }
+}
+
+/* Statistics of one pair (m, l) whose grid is chi[D][L] plus the rank-one
+ * term dk[d] * ej[j] (dk = NULL: unperturbed).  Rows are reduced in order. */
+static fd_stat fd_pair_stat(const or_cfg* c, int m, int l, const cplx* chi, const cplx* dk, const cplx* ej,
+                            double* rmax, double* rsum)
+{
+    int L = c->L, D = c->k_hi - c->k_lo + 1;
+#pragma omp parallel for schedule(static)
+    for (int d = 0; d < D; ++d) {
+        rmax[d] = -1.0; rsum[d] = 0.0;
+        if (cell_class(m, l, c->k_lo + d) < 0) continue;
+        const cplx* row = chi + (size_t)d * L;
+        double vm = -1.0;
+        for (int j = 0; j < L; ++j) {
+            double w = cell_weight(c, d, j);
+            if (w <= 0) continue;
+            cplx a = dk ? row[j] + dk[d] * ej[j] : row[j];
+            double v = w * cabs(a);
+            if (v > vm) vm = v;
+        }
+        rmax[d] = vm;
+        if (c->pnorm > 0 && vm > 0) {
+            double s = 0;
+            for (int j = 0; j < L; ++j) {
+                double w = cell_weight(c, d, j);
+                if (w <= 0) continue;
+                cplx a = dk ? row[j] + dk[d] * ej[j] : row[j];
+                s += pow(w * cabs(a) / vm, c->pnorm);
+            }
+            rsum[d] = s;
+        }
+    }
+    fd_stat st = { 0.0, 0.0, 0 };
+    for (int d = 0; d < D; ++d)
+        if (rmax[d] >= 0) fd_fold(c->pnorm, &st, rmax[d], rsum[d]);
+    return st;
+}
+
+void or_fd_losses(int M, int N, int L, const double* nu, int k_lo, int k_hi,
+                  const double* w, double eps, double snrl_db, double pnorm,
+                  const double* x_ri, const double* h_ri, int ncoord,
+                  const int* target, const int* row, const int* col,
+                  const double* vp_ri, const double* vm_ri,
+                  double* loss_p, double* loss_m)
+{
+    or_cfg c = { M, N, L, k_lo, k_hi, nu, w, eps, snrl_db, pnorm };
+    const cplx* x = (const cplx*)x_ri;
+    const cplx* h = (const cplx*)h_ri;
+    const cplx* vp = (const cplx*)vp_ri;
+    const cplx* vmn = (const cplx*)vm_ri;
+    int D = k_hi - k_lo + 1, P = M * M;
+    cplx* E = phasor_table(N, L, nu);
+    cplx* chi = (cplx*)malloc(sizeof(cplx) * (size_t)D * L);
+    cplx* dk = (cplx*)malloc(sizeof(cplx) * (size_t)D);
+    cplx* ej = (cplx*)malloc(sizeof(cplx) * (size_t)L);
+    double* rmax = (double*)malloc(sizeof(double) * D);
+    double* rsum = (double*)malloc(sizeof(double) * D);
+    fd_stat* base = (fd_stat*)calloc((size_t)P, sizeof(fd_stat));
+    fd_stat* pert = (fd_stat*)calloc((size_t)ncoord * 2 * P, sizeof(fd_stat));
+
+    for (int pair = 0; pair < P; ++pair) {
+        int m = pair / M, l = pair % M;
+        /* Eq. 6 on every cell of this pair */
+#pragma omp parallel for schedule(static)
+        for (int d = 0; d < D; ++d)
+            for (int j = 0; j < L; ++j)
+                chi[(size_t)d * L + j] = af_cell_tab(N, x + (size_t)m * N, h + (size_t)l * N, k_lo + d,
+                                                     E + (size_t)j * N);
+        base[pair] = fd_pair_stat(&c, m, l, chi, NULL, NULL, rmax, rsum);
+        for (int ci = 0; ci < ncoord; ++ci) {
+            int r = row[ci], n0 = col[ci];
+            int touches = (target[ci] == 0) ? (r == m) : (r == l);
+            if (!touches) continue;
+            for (int side = 0; side < 2; ++side) {
+                cplx v = side == 0 ? vp[ci] : vmn[ci];
+                if (target[ci] == 0) {
+                    cplx delta = v - x[(size_t)m * N + n0];
+                    for (int d = 0; d < D; ++d) {
+                        int q = n0 + k_lo + d;
+                        dk[d] = (q >= 0 && q < N) ? delta * conj(h[(size_t)l * N + q]) : 0.0;
+                    }
+                    for (int j = 0; j < L; ++j) ej[j] = E[(size_t)j * N + n0];
+                } else {
+                    /* h_l(p0) changes: the sample n = p0 - k of row k, phasor e^{j 2 pi nu n} */
+                    cplx delta = v - h[(size_t)l * N + n0];
+                    for (int d = 0; d < D; ++d) dk[d] = 0.0;
+                    /* the phasor depends on n = p0 - k, so the term is not a product of a
+                     * row factor and a column factor: handle it row by row */
+                    fd_stat st = { 0.0, 0.0, 0 };
+#pragma omp parallel for schedule(static)
+                    for (int d = 0; d < D; ++d) {
+                        int k = k_lo + d, n = n0 - k;
+                        rmax[d] = -1.0; rsum[d] = 0.0;
+                        if (cell_class(m, l, k) < 0) continue;
+                        cplx a0 = (n >= 0 && n < N) ? x[(size_t)m * N + n] * conj(delta) : 0.0;
+                        const cplx* row_ = chi + (size_t)d * L;
+                        double vmx = -1.0;
+                        for (int j = 0; j < L; ++j) {
+                            double wt = cell_weight(&c, d, j);
+                            if (wt <= 0) continue;
+                            cplx a = (n >= 0 && n < N) ? row_[j] + a0 * E[(size_t)j * N + n] : row_[j];
+                            double vv = wt * cabs(a);
+                            if (vv > vmx) vmx = vv;
+                        }
+                        rmax[d] = vmx;
+                        if (pnorm > 0 && vmx > 0) {
+                            double s = 0;
+                            for (int j = 0; j < L; ++j) {
+                                double wt = cell_weight(&c, d, j);
+                                if (wt <= 0) continue;
+                                cplx a = (n >= 0 && n < N) ? row_[j] + a0 * E[(size_t)j * N + n] : row_[j];
+                                s += pow(wt * cabs(a) / vmx, pnorm);
+                            }
+                            rsum[d] = s;
+                        }
+                    }
+                    for (int d = 0; d < D; ++d)
+                        if (rmax[d] >= 0) fd_fold(pnorm, &st, rmax[d], rsum[d]);
+                    pert[((size_t)ci * 2 + side) * P + pair] = st;
+                    continue;
+                }
+                pert[((size_t)ci * 2 + side) * P + pair] = fd_pair_stat(&c, m, l, chi, dk, ej, rmax, rsum);
+            }
+        }
+    }
+
+    double ptar = pow(10.0, -snrl_db / 20.0);                       /* Eq. 39 */
+    for (int ci = 0; ci < ncoord; ++ci) {
+        for (int side = 0; side < 2; ++side) {
+            fd_stat cls[2] = { { 0.0, 0.0, 0 }, { 0.0, 0.0, 0 } };
+            for (int pair = 0; pair < P; ++pair) {
+                int m = pair / M, l = pair % M;
+                int touched = (target[ci] == 0) ? (row[ci] == m) : (row[ci] == l);
+                const fd_stat* s = touched ? &pert[((size_t)ci * 2 + side) * P + pair] : &base[pair];
+                if (s->any) fd_fold(pnorm, &cls[m == l ? 0 : 1], s->vmax, s->psum);
+            }
+            double v[2];
+            for (int k = 0; k < 2; ++k) {                             /* Eqs. 8-9 (or their p-norms) */
+                if (!cls[k].any) v[k] = 0.0;
+                else if (pnorm > 0) v[k] = cls[k].vmax * pow(cls[k].psum, 1.0 / pnorm);
+                else v[k] = cls[k].vmax;
+            }
+            double lw = v[0] >= v[1] ? v[0] : v[1];                   /* Eq. 37 */
+            cplx nv = side == 0 ? vp[ci] : vmn[ci];
+            double ls = 0;
+            for (int m = 0; m < M; ++m) {
+                cplx a00 = 0;
+                for (int n = 0; n < N; ++n) {
+                    cplx xv = x[(size_t)m * N + n], hv = h[(size_t)m * N + n];
+                    if (m == row[ci] && n == col[ci]) {
+                        if (target[ci] == 0) xv = nv; else hv = nv;
+                    }
+                    a00 += conj(hv) * xv;
+                }
+                double dev = cabs(a00) / (double)N - ptar;            /* Eq. 38 */
+                ls += dev * dev;
+            }
+            ls /= (double)M;                                          /* Eq. 41 */
+            double loss = eps * lw + (1.0 - eps) * ls;                /* Eq. 42 */
+            if (side == 0) loss_p[ci] = loss; else loss_m[ci] = loss;
+        }
+    }
+    free(E); free(chi); free(dk); free(ej); free(rmax); free(rsum); free(base); free(pert);
 }

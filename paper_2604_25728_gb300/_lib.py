@@ -52,6 +52,10 @@ class AfState(ctypes.Structure):
     ]
 
 
+class AfStop(ctypes.Structure):
+    _fields_ = [("best_wpsl", c_double), ("best_outer", c_int64), ("stopped", c_int32)]
+
+
 class WsConfig(ctypes.Structure):
     _fields_ = [("M", c_int32), ("N", c_int32), ("B", c_int32), ("cond", c_double * 5)]
 
@@ -76,6 +80,10 @@ SIGNATURES = {
     "af_project_thresholds": (c_int32, [c_void_p, c_void_p]),
     "sqngd_init": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sqngd_step": (c_int32, [c_void_p, ctypes.POINTER(AfState), c_int32, P_double]),
+    "sqngd_run": (c_int32, [c_void_p, ctypes.POINTER(AfState), c_int64, c_int32, ctypes.POINTER(AfStop),
+                            P_double, ctypes.POINTER(c_int64)]),
+    "af_get_rho_state": (c_int32, [c_void_p, P_float, P_float, P_float, ctypes.POINTER(c_int32)]),
+    "af_set_rho_state": (c_int32, [c_void_p, P_float, P_float, P_float, c_int32]),
     "af_eval_hard": (c_int32, [c_void_p, c_void_p, c_void_p, P_double]),
     "af_loss_terms_noalloc": (c_int32, [c_int32, c_int32, c_int32, c_double, c_int32, c_int32, c_double, c_double,
                                         c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -85,6 +93,8 @@ SIGNATURES = {
     "rn_last_error": (ctypes.c_char_p, [c_void_p]),
     "rn_set_params": (c_int32, [c_void_p, P_float]),
     "rn_get_params": (c_int32, [c_void_p, P_float]),
+    "rn_set_adam": (c_int32, [c_void_p, P_float, P_float]),
+    "rn_get_adam": (c_int32, [c_void_p, P_float, P_float]),
     "rn_forward": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "rn_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
     "sqngd_attach_generator": (c_int32, [c_void_p, c_void_p, c_void_p]),

@@ -7,7 +7,7 @@ kernels.  PyTorch provides device memory and the stream.
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass
+from dataclasses import dataclass, field
 from typing import Optional
 
 import numpy as np
@@ -201,6 +201,41 @@ class Context:
         state.t_h, state.t_x, state.outer = cs.t_h, cs.t_x, cs.outer
         return buf
 
+    def sqngd_run(self, state: "SqngdState", t_max: int, patience: int = 50, log: bool = True):
+        """Outer iterations until Algorithm 1's stopping test fires (no better
+        hard WPSL for `patience` iterations) or state.outer reaches t_max.
+        Returns (log [n_done, evals, 4] or None, the stopped code: 1 patience,
+        2 t_max).  The rule's record lives in state.stop (kept by save/load)."""
+        cs = state.c_struct()
+        stop = _lib.AfStop(best_wpsl=float(state.stop[0]), best_outer=int(state.stop[1]), stopped=0)
+        evals = (1 + self.n_x) if self.matched else (self.n_h + self.n_x)
+        rows = max(0, int(t_max) - int(state.outer))
+        buf = np.zeros((rows, evals, 4), dtype=np.float64) if log else None
+        done = ctypes.c_int64(0)
+        self._check(self.lib.sqngd_run(self.handle, ctypes.byref(cs), int(t_max), int(patience), ctypes.byref(stop),
+                                       None if buf is None else buf.ctypes.data_as(_lib.P_double),
+                                       ctypes.byref(done)))
+        state.t_h, state.t_x, state.outer = cs.t_h, cs.t_x, cs.outer
+        state.stop = [stop.best_wpsl, stop.best_outer]
+        return (None if buf is None else buf[:done.value]), int(stop.stopped)
+
+    def get_rho_state(self):
+        """(rho, m_rho, v_rho, uniform) of the quantization thresholds."""
+        r, m, v = (np.zeros(self.K, dtype=np.float32) for _ in range(3))
+        uni = ctypes.c_int32(0)
+        self._check(self.lib.af_get_rho_state(self.handle, r.ctypes.data_as(_lib.P_float),
+                                              m.ctypes.data_as(_lib.P_float), v.ctypes.data_as(_lib.P_float),
+                                              ctypes.byref(uni)))
+        return r, m, v, int(uni.value)
+
+    def set_rho_state(self, rho, m_rho, v_rho, uniform: int):
+        r, m, v = (np.ascontiguousarray(a, dtype=np.float32) for a in (rho, m_rho, v_rho))
+        if not (r.size == m.size == v.size == self.K):
+            raise ValueError(f"need K = {self.K} thresholds and moments")
+        self._check(self.lib.af_set_rho_state(self.handle, r.ctypes.data_as(_lib.P_float),
+                                              m.ctypes.data_as(_lib.P_float), v.ctypes.data_as(_lib.P_float),
+                                              int(uniform)))
+
     def af_eval_hard(self, u, h):
         self._mn(u, "u"); h = self._filters(h)
         out = np.zeros(4 + self.M, dtype=np.float64)
@@ -254,6 +289,22 @@ class ResNetGenerator:
         self._check(self.lib.rn_get_params(self.handle, t.ctypes.data_as(_lib.P_float)), self.handle)
         return t
 
+    def get_adam(self):
+        """The Adam moments (m, v) of every parameter."""
+        m = np.zeros(self.param_count(self.P), dtype=np.float32)
+        v = np.zeros_like(m)
+        self._check(self.lib.rn_get_adam(self.handle, m.ctypes.data_as(_lib.P_float),
+                                         v.ctypes.data_as(_lib.P_float)), self.handle)
+        return m, v
+
+    def set_adam(self, m, v):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        if m.size != self.param_count(self.P) or v.size != m.size:
+            raise ValueError("wrong moment count")
+        self._check(self.lib.rn_set_adam(self.handle, m.ctypes.data_as(_lib.P_float),
+                                         v.ctypes.data_as(_lib.P_float)), self.handle)
+
     def forward(self, y0, u=None):
         _need(y0, torch.float32, (self.P,), "y0")
         u = torch.empty(self.P, dtype=torch.float32, device=self.device) if u is None else u
@@ -284,6 +335,8 @@ class SqngdState:
     t_h: int = 0
     t_x: int = 0
     outer: int = 0
+    # record of the stopping rule (sqngd_run): best hard WPSL so far and its outer iteration
+    stop: list = field(default_factory=lambda: [float("inf"), -1])
 
     @classmethod
     def create(cls, u, h=None):
@@ -298,21 +351,42 @@ class SqngdState:
 
     _BUFFERS = ("u", "h", "m_u", "v_u", "m_h", "v_h", "best_q", "best_h", "best")
 
-    def save(self, path: str):
-        """Checkpoint every buffer of the state and the step counters to an
-        .npz file.  The context's own state is not included: thresholds set
-        by af_set_thresholds or trained (read them with af_get_thresholds),
-        the thresholds' Adam moments, and an attached generator's parameters
-        (rn_get_params) and moments."""
+    def save(self, path: str, ctx: Optional["Context"] = None, generator: Optional["ResNetGenerator"] = None):
+        """Checkpoint every buffer of the state, the step counters and the
+        stopping-rule record to an .npz file; with `ctx`, also the context's
+        threshold state (rho, its Adam moments, uniform flag); with
+        `generator`, the attached generator's parameters and Adam moments."""
         arrays = {k: getattr(self, k).detach().cpu().numpy() for k in self._BUFFERS if getattr(self, k) is not None}
-        np.savez(path, t_h=np.int64(self.t_h), t_x=np.int64(self.t_x), outer=np.int64(self.outer), **arrays)
+        if ctx is not None:
+            r, m, v, uni = ctx.get_rho_state()
+            arrays.update(rho=r, m_rho=m, v_rho=v, rho_uniform=np.int32(uni))
+        if generator is not None:
+            gm, gv = generator.get_adam()
+            arrays.update(gen_theta=generator.get_params(), gen_m=gm, gen_v=gv)
+        np.savez(path, t_h=np.int64(self.t_h), t_x=np.int64(self.t_x), outer=np.int64(self.outer),
+                 stop_best=np.float64(self.stop[0]), stop_outer=np.int64(self.stop[1]), **arrays)
 
     @classmethod
-    def load(cls, path: str, device=None):
-        """The state saved by `save`, with its buffers on `device`."""
+    def load(cls, path: str, device=None, ctx: Optional["Context"] = None,
+             generator: Optional["ResNetGenerator"] = None, y0=None):
+        """The state saved by `save`, with its buffers on `device`; with `ctx`
+        and `generator`, their saved parts are restored into them (the file
+        must hold them).  A generator's next training step uses the
+        activations of its last forward pass, so with `generator` pass its
+        input y0 as well: the forward pass is rerun at the restored
+        parameters."""
         with np.load(path) as f:
             t = {k: (torch.from_numpy(f[k]).to(device) if k in f.files else None) for k in cls._BUFFERS}
-            return cls(**t, t_h=int(f["t_h"]), t_x=int(f["t_x"]), outer=int(f["outer"]))
+            stop = [float(f["stop_best"]), int(f["stop_outer"])] if "stop_best" in f.files else [float("inf"), -1]
+            if ctx is not None:
+                ctx.set_rho_state(f["rho"], f["m_rho"], f["v_rho"], int(f["rho_uniform"]))
+            if generator is not None:
+                if y0 is None:
+                    raise ValueError("restoring a generator needs its input y0")
+                generator.set_params(f["gen_theta"])
+                generator.set_adam(f["gen_m"], f["gen_v"])
+                generator.forward(y0)
+            return cls(**t, t_h=int(f["t_h"]), t_x=int(f["t_x"]), outer=int(f["outer"]), stop=stop)
 
     def c_struct(self):
         p = lambda t: 0 if t is None else t.data_ptr()
@@ -323,22 +397,27 @@ class SqngdState:
 
 
 class AfLoss(torch.autograd.Function):
-    """Loss of Eq. 42 through the soft transmit chain; backward returns the
-    gradient the library's adjoint computed in the same call (scaled by the
-    incoming gradient)."""
+    """Loss of Eq. 42 through the soft transmit chain as a
+    torch.autograd.Function.  The forward pass evaluates the loss alone (no
+    adjoint, no gradient buffers) and keeps only u and h; the backward pass
+    calls the library again with gradient outputs, so the hand-written
+    adjoint recomputes the products and spectra it needs instead of storing
+    them, and scales its gradient by the incoming one."""
 
     @staticmethod
     def forward(fctx, u, h, ctx: Context):
-        gu = torch.empty_like(u)
-        gh = torch.empty_like(h)
-        terms, _, _ = ctx.af_loss_grad(u.detach().contiguous(), h.detach().contiguous(), False,
-                                       grad_u=gu, grad_h=gh)
-        fctx.save_for_backward(gu, gh)
+        u_, h_ = u.detach().contiguous(), h.detach().contiguous()
+        terms, _, _ = ctx.af_loss_grad(u_, h_, False)
+        fctx.save_for_backward(u_, h_)
+        fctx.af_ctx = ctx
         return terms[0].clone()
 
     @staticmethod
     def backward(fctx, g):
-        gu, gh = fctx.saved_tensors
+        u, h = fctx.saved_tensors
+        gu = torch.empty_like(u)
+        gh = torch.empty_like(h)
+        fctx.af_ctx.af_loss_grad(u, h, False, grad_u=gu, grad_h=gh)
         s = g.to(torch.float32)
         return gu * s, gh * s, None
 

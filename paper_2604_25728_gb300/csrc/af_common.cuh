@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <utility>
 
 namespace af {
@@ -62,21 +63,36 @@ __device__ __forceinline__ DFloat df_warp_sum(DFloat a) {
 }
 __device__ __forceinline__ double df_to_double(DFloat a) { return (double)a.hi + (double)a.lo; }
 
+// The product of two FP32 values as an unevaluated pair p + e, exactly
+// (Dekker's TwoProduct with a fused multiply-add: e = fma(a, b, -p) is the
+// rounding error of p = a b, representable because an FP32 product has at
+// most 48 significant bits).
+__device__ __forceinline__ DFloat df_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// Accumulate sum_n x(n) conj(h(n)) = (xr hr + xi hi) + j (xi hr - xr hi)
+// with every product exact and the sums in double-float.
+__device__ __forceinline__ void df_acc_xconjh(float2 xv, float2 hv, DFloat& sr, DFloat& si) {
+    sr = df_add(sr, df_two_prod(xv.x, hv.x));
+    sr = df_add(sr, df_two_prod(xv.y, hv.y));
+    si = df_add(si, df_two_prod(xv.y, hv.x));
+    si = df_add(si, df_two_prod(-xv.x, hv.y));
+}
+
 // chi_mm(0, 0) = sum_n x(n) conj(h(n)) (Eq. 38) by the NT threads of a CTA
-// (all of them call it; it synchronises the CTA once): FP32 products and
-// per-thread partials, then a double-float tree; thread 0 stores the sum.
+// (all of them call it; it synchronises the CTA once): exact FP32 products,
+// per-thread double-float partials, then a double-float tree (about 44
+// significant bits in all); thread 0 stores the sum.
 template <int NT>
 __device__ __forceinline__ void diag_sum_f32(const float2* __restrict__ x, const float2* __restrict__ h, int N,
                                              double2* out) {
     __shared__ DFloat red[2][NT / 32];
     const int tid = threadIdx.x;
-    float sr = 0.f, si = 0.f;
-    for (int n = tid; n < N; n += NT) {
-        const float2 xv = x[n], hv = h[n];
-        sr = fmaf(xv.x, hv.x, fmaf(xv.y, hv.y, sr));
-        si = fmaf(xv.y, hv.x, fmaf(-xv.x, hv.y, si));
-    }
-    const DFloat r = df_warp_sum({sr, 0.f}), i = df_warp_sum({si, 0.f});
+    DFloat sr = {0.f, 0.f}, si = {0.f, 0.f};
+    for (int n = tid; n < N; n += NT) df_acc_xconjh(x[n], h[n], sr, si);
+    const DFloat r = df_warp_sum(sr), i = df_warp_sum(si);
     if ((tid & 31) == 0) { red[0][tid >> 5] = r; red[1][tid >> 5] = i; }
     __syncthreads();
     if (tid == 0) {
@@ -277,13 +293,16 @@ namespace af {
 // Raise a kernel's dynamic shared-memory limit to the largest size requested
 // so far on the current device (no-op afterwards, so it is safe to call while
 // a stream is being captured once the first uncaptured launch has happened).
+// The table is shared by every host thread and guarded by a lock.
 inline cudaError_t set_smem_once(const void* func, int bytes) {
     struct Entry { const void* f; int dev; int bytes; };
     static Entry table[256];
     static int n = 0;
+    static std::mutex mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
     for (int i = 0; i < n; ++i)
         if (table[i].f == func && table[i].dev == dev && table[i].bytes >= bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

@@ -15,7 +15,8 @@
 // dL/du = 2 pi Im(conj(x) grad x) Q_A'(z) z(1-z).  With matched filters
 // (SQNAF, h = x) the waveform takes both partial gradients, grad x + grad h.
 // In the optimiser modes the CTA applies Adam to its strip; for the filters
-// the projection of Eq. 32 needs the row's norm: every strip puts its FP64 partial in shared memory,
+// the projection of Eq. 32 needs the row's norm: every strip puts its double-float partial (sums of
+// exact FP32 squares) in shared memory,
 // the cluster synchronises, and every CTA sums the partials of its cluster in
 // rank order through distributed shared memory (same sum everywhere, no
 // global round trip).  A CTA reads other rows only in the gradient gather,
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     __shared__ float2 sc2[2][kNW];
     __shared__ float spv[2][kNW], sps[2][kNW];
     __shared__ float s_terms[8];
-    __shared__ float s_pmin2;
+    __shared__ double s_pmin2;       // min_m p_m^2 (FP64)
+    __shared__ double s_ls64;        // L_SNRL (Eq. 41, FP64)
+    __shared__ double s_loss64;      // L (Eq. 42, FP64 assembly)
     __shared__ float2 s_g;           // sparse coefficient g
     __shared__ int s_cell[4];        // m*, l*, k*, j*  (m* = -1: no sparse term)
     __shared__ float2 s_G;           // SNRL coefficient of row m
@@ -124,8 +127,12 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     if (!dry) pdl_wait();
 
     // ---- 1. one batch of loads of everything the previous kernels wrote -------
+    // The last warp takes the SNRL term (FP64) while the others merge the
+    // forward partials, so its FP64 latency stays off the critical path.
+    const int SW = NW - 1;           // SNRL warp (NW >= 4)
+    const int NMT = SW * 32;         // merging threads
     double2 cm = make_double2(0.0, 0.0);
-    if (warp == 0 && lane < M) cm = __ldcg(a.cdiag + lane);
+    if (warp == SW && lane < M) cm = __ldcg(a.cdiag + lane);
     constexpr bool kSnap = (MODE == FIN_ADAM_H || MODE == FIN_SCORE);   // may take the best-design record
     const bool opt = (MODE == FIN_ADAM_H || MODE == FIN_ADAM_U || MODE == FIN_SCORE) && a.ctr != nullptr;
     long long cv0 = 0, cv1 = 0, cv2 = 0, cv3 = 0;
@@ -139,13 +146,13 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     float2 cb[2] = {zero2, zero2};
     float pv[2] = {0.f, 0.f}, ps[2] = {0.f, 0.f};
     constexpr int U = 4;   // partials loaded per thread before any is compared
-    for (int b0 = 0; b0 < a.nblk; b0 += U * (int)blockDim.x) {
+    for (int b0 = 0; warp < SW && b0 < a.nblk; b0 += U * NMT) {
         long long ids[U];
         float ks[U], vv[U], ss[U];
         float2 cs[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int b = b0 + u * (int)blockDim.x + tid;
+            const int b = b0 + u * NMT + tid;
             const bool ok = b < a.nblk;
             ids[u] = ok ? __ldcg(a.pidx + b) : -1;
             ks[u] = ok ? __ldcg(a.pkey + b) : -1.f;
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (ids[u] < 0) continue;
-            const int pair = (b0 + u * (int)blockDim.x + tid) / a.ctas_per_pair;
+            const int pair = (b0 + u * NMT + tid) / a.ctas_per_pair;
             const int cls = (pair / M == pair % M) ? 0 : 1;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {            // static indices: the class arrays stay in registers
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         }
     }
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < 2 && warp < SW; ++c) {
         for (int o = 16; o > 0; o >>= 1) {
             const float ok = __shfl_xor_sync(0xffffffffu, kb[c], o);
             const long long oi = __shfl_xor_sync(0xffffffffu, ib[c], o);
@@ -178,38 +185,37 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             const float os = __shfl_xor_sync(0xffffffffu, ps[c], o);
             if constexpr (PN) pmerge(a.half_p, pv[c], ps[c], ov, os);
         }
-        if (lane == 0) {
+        if (lane == 0 && warp < SW) {
             sk[c][warp] = kb[c]; si[c][warp] = ib[c]; sc2[c][warp] = cb[c];
             spv[c][warp] = pv[c]; sps[c][warp] = ps[c];
         }
     }
 
-    // ---- 2. SNRL term, one waveform per lane of warp 0 (FP32); counters -------
-    if (warp == 0) {
-        // A_mm(0,0) arrives as a double-float sum; p_m and L_SNRL need no more
-        // than FP32 (relative error ~1e-7), and FP64 here would put dependent
-        // FP64 operations on every evaluation's critical path
-        const float cr = (float)cm.x, ci = (float)cm.y;
-        const float c2 = cr * cr + ci * ci;
-        const float p = (lane < M) ? sqrtf(c2) * a.inv_N_f : 0.f;   // p_m = |A_mm(0,0)| / N (Eq. 38)
-        const float dev = p - a.ptar_f;
-        float ls = (lane < M) ? dev * dev : 0.f;
-        float pmin2 = (lane < M) ? c2 * a.inv_N_f * a.inv_N_f : 3.0e38f;
+    // ---- 2. SNRL term in FP64, one waveform per lane of the last warp; counters
+    if (warp == SW) {
+        // A_mm(0,0) arrives as a double-float sum of exact products (~44 bits);
+        // p_m, L_SNRL and the SNRL gradient coefficient are formed in FP64
+        const double cr = cm.x, ci = cm.y;
+        const double c2 = cr * cr + ci * ci;
+        const double p = (lane < M) ? sqrt(c2) * a.inv_N : 0.0;    // p_m = |A_mm(0,0)| / N (Eq. 38)
+        const double dev = p - a.ptar;
+        double ls = (lane < M) ? dev * dev : 0.0;
+        double pmin2 = (lane < M) ? c2 * a.inv_N * a.inv_N : 1.0e300;
         for (int o = 16; o > 0; o >>= 1) {
             ls += __shfl_xor_sync(0xffffffffu, ls, o);
-            pmin2 = fminf(pmin2, __shfl_xor_sync(0xffffffffu, pmin2, o));
+            pmin2 = fmin(pmin2, __shfl_xor_sync(0xffffffffu, pmin2, o));
         }
         if (lane == m) {
             // G_m = (1-eps)(2/M)(p_m - p_tar)/N * c_m/|c_m|
-            const float mag = p * (float)N;
-            const float coef = (mag > 0.f) ? a.snrl_coef_f * dev / mag : 0.f;
-            s_G = make_float2(coef * cr, coef * ci);
+            const double mag = p * (double)N;
+            const double coef = (mag > 0.0) ? a.snrl_coef * dev / mag : 0.0;
+            s_G = make_float2((float)(coef * cr), (float)(coef * ci));
         }
         if (lane == 0) {
-            s_terms[4] = ls * a.inv_M_f;                   // L_SNRL (Eq. 41)
+            s_ls64 = ls / (double)M;                       // L_SNRL (Eq. 41)
             s_pmin2 = pmin2;
         }
-        if (!dry && m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = (double)p;
+        if (!dry && m == 0 && blockIdx.x == 0 && a.terms != nullptr && lane < M) a.terms[8 + lane] = p;
     } else if (warp == 1 && opt) {
         if (lane == 0) {
             s_ctr[0] = cv0; s_ctr[1] = cv1; s_ctr[2] = cv2; s_ctr[3] = cv3;
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
             long long i = si[c][0];
             float2 x = sc2[c][0];
             float v = spv[c][0], sm = sps[c][0];
-            for (int w = 1; w < NW; ++w) {
+            for (int w = 1; w < SW; ++w) {
                 if (fbetter(sk[c][w], si[c][w], k, i)) { k = sk[c][w]; i = si[c][w]; x = sc2[c][w]; }
                 if constexpr (PN) pmerge(a.half_p, v, sm, spv[c][w], sps[c][w]);
             }
@@ -250,8 +256,8 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         const float lw = cls ? cvv[1] : cvv[0];
         const long long cell_w = cls ? cell[1] : cell[0];
         const float2 chi_w = cls ? chi[1] : chi[0];
-        const float ls = s_terms[4];
-        s_terms[0] = a.eps_f * lw + (1.f - a.eps_f) * ls;   // Eq. 42
+        const double ls = s_ls64;
+        s_loss64 = a.eps * (double)lw + (1.0 - a.eps) * ls;   // Eq. 42
         s_terms[1] = lw; s_terms[2] = cvv[0]; s_terms[3] = cvv[1];
         // winning cell of the exact max and its coefficient g = eps w chi/|chi|
         s_cell[0] = -1;
@@ -287,14 +293,16 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
         const long long o = opt ? s_ctr[0] - 1 : 0;
         if (!dry && m == 0 && blockIdx.x == 0) {
             if (a.terms) {
-                for (int i = 0; i < 5; ++i) a.terms[i] = (double)s_terms[i];
+                a.terms[0] = s_loss64;
+                for (int i = 1; i < 4; ++i) a.terms[i] = (double)s_terms[i];
+                a.terms[4] = ls;
                 a.terms[5] = (double)cls; a.terms[6] = (double)cell[0]; a.terms[7] = (double)cell[1];
             }
             if (a.log) {
                 double* lg = a.log + ((size_t)o * a.evals_per_outer + a.eval_index) * 4;
-                lg[0] = (double)s_terms[0]; lg[1] = (double)lw; lg[2] = (double)ls; lg[3] = (double)cls;
+                lg[0] = s_loss64; lg[1] = (double)lw; lg[2] = ls; lg[3] = (double)cls;
             }
-            if (!isfinite(s_terms[0]) && a.err_flag) atomicOr(a.err_flag, 1);
+            if (!isfinite(s_loss64) && a.err_flag) atomicOr(a.err_flag, 1);
         }
         if (opt) {
             s_ok = 0;
@@ -303,11 +311,11 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 const double* prev = s_best + ((o + 1) & 1) * 4;
                 double* cur = a.best2 + (o & 1) * 4;
                 // SNRL_m = -20 log10 p_m <= target + 0.05 dB  <=>  p_m^2 >= p_accept2
-                s_ok = (s_pmin2 >= a.p_accept2_f && (double)lw < prev[0]) ? 1 : 0;
+                s_ok = (s_pmin2 >= a.p_accept2 && (double)lw < prev[0]) ? 1 : 0;
                 if (!dry && m == 0 && blockIdx.x == 0) {
                     if (s_ok) {
-                        cur[0] = (double)lw; cur[1] = (double)s_terms[0];
-                        cur[2] = (double)(s_ctr[3] + o); cur[3] = (double)(-10.f * log10f(s_pmin2));
+                        cur[0] = (double)lw; cur[1] = s_loss64;
+                        cur[2] = (double)(s_ctr[3] + o); cur[3] = -10.0 * log10(s_pmin2);
                     } else {
                         for (int i = 0; i < 4; ++i) cur[i] = prev[i];
                     }
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
     if (MODE == FIN_ADAM_H) {
         // Adam on (H_Re, H_Im), then the projection of Eq. 32 with the row's norm
         float2 hv[EPT];
-        float e2 = 0.f;
+        DFloat e2 = {0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < EPT; ++i) {
             const int n = n_base + tid + i * kFT;
@@ -412,10 +420,11 @@ __global__ void __launch_bounds__(kFT, 1) fin_kernel(const FinArgs a) {
                 a.v_h[e] = vv;
             }
             hv[i] = h_;
-            e2 = fmaf(h_.x, h_.x, fmaf(h_.y, h_.y, e2));
+            e2 = df_add(e2, df_add(df_two_prod(h_.x, h_.x), df_two_prod(h_.y, h_.y)));
         }
-        // ||h_m||^2 as a double-float tree: warps, then the strips of the cluster
-        const DFloat wsum = df_warp_sum({e2, 0.f});
+        // ||h_m||^2 from exact squares as a double-float tree: warps, then the
+        // strips of the cluster (about 44 significant bits)
+        const DFloat wsum = df_warp_sum(e2);
         if (lane == 0) shd[warp] = wsum;
         __syncthreads();
         if (tid == 0) {
@@ -518,11 +527,6 @@ static cudaError_t launch_mode(const cudaLaunchConfig_t& cfg, const FinArgs& a, 
 cudaError_t launch_fin(const FinArgs& a_in, cudaStream_t s) {
     FinArgs a = a_in;
     a.eps_f = (float)a.eps;
-    a.ptar_f = (float)a.ptar;
-    a.inv_N_f = (float)a.inv_N;
-    a.snrl_coef_f = (float)a.snrl_coef;
-    a.inv_M_f = (float)(1.0 / a.M);
-    a.p_accept2_f = (float)a.p_accept2;
     const int T = fin_threads(a.N);
     const int S = (a.N + T - 1) / T;
     if (S > kMaxStrips) return cudaErrorInvalidValue;   // N > 4096 is rejected by the host checks

@@ -145,8 +145,8 @@ fwd_gemm_kernel(const GemmArgs g) {
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    // CTAs are ordered pair-group-fastest, so the CTAs of a cluster share the
-    // delay block and column tile -- hence every B image -- and differ in pairs.
+    // CTAs are ordered pair-group-fastest: consecutive CTAs share the delay
+    // block and column tile -- hence every B image, which they read from L2.
     // A CTA owns the T consecutive pairs pg*T .. pg*T + T-1 of one delay block.
     const int bx = blockIdx.x;
     const int P = a.M * a.M;
@@ -162,15 +162,11 @@ fwd_gemm_kernel(const GemmArgs g) {
     const int n_begin = max(0, -k_last), n_end = min(N, N - k_first);
     const int c0 = n_begin / kSPC;
     const int nch = (n_end + kSPC - 1) / kSPC - c0;
-    const int C = g.csize;
-    const uint32_t crank = (C > 1) ? tc::cluster_ctarank() : 0u;
-    const uint16_t cmask = (uint16_t)((1u << C) - 1u);
-    const int SLB = STAGE_BYTES / C;                           // this CTA's slice of every stage
 
     if (tid == 0) {
         for (int s = 0; s < kSB; ++s) {
             tc::mbar_init(&bfull[s], 1);
-            tc::mbar_init(&bempty[s], C);   // one MMA commit from every CTA of the cluster
+            tc::mbar_init(&bempty[s], 1);   // one MMA commit
         }
         for (int s = 0; s < kSA; ++s) {
             tc::mbar_init(&afull[s], NPROD / 32);   // one arrival per producer warp
@@ -187,8 +183,7 @@ fwd_gemm_kernel(const GemmArgs g) {
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
-    if (C > 1) tc::cluster_sync();   // barriers initialised cluster-wide before any multicast
-    else __syncthreads();
+    __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = s_tmem;
     volatile int* abort_flag = &s_abort;
@@ -198,15 +193,10 @@ fwd_gemm_kernel(const GemmArgs g) {
 
     if (warp == WLOAD) {
         // ---------------------------------------------------- B loader --
-        // Stage s of chunk i: this CTA expects the whole stage on its own
-        // barrier and copies its slice into every CTA of the cluster.
+        // Stage s of chunk i: one bulk copy of the whole stage, completing on bfull[s].
         auto issue = [&](int i, int s) {
             tc::mbar_arrive_expect_tx(&bfull[s], STAGE_BYTES);
-            if (C > 1)
-                tc::bulk_g2s_mc(bst + s * STAGE_BYTES + crank * SLB, img + (size_t)i * STAGE_BYTES + crank * SLB,
-                                SLB, &bfull[s], cmask);
-            else
-                tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
+            tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
         };
         int issued = 0;
         if (lane == 0) {
@@ -221,13 +211,13 @@ fwd_gemm_kernel(const GemmArgs g) {
         if (lane == 0) {
             for (int i = kSB; i < nch; ++i) {
                 const int s = i % kSB;
-                // every CTA of the cluster has finished with stage s
+                // the MMAs have finished with stage s
                 if (!gwait(&bempty[s], ((i / kSB) - 1) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
                 issue(i, s);
                 issued = i + 1;
             }
-            // every stage this CTA expects has landed, and every MMA commit
-            // the cluster sends to this CTA has arrived, before it exits
+            // every stage in flight has landed, and every MMA commit has
+            // arrived, before the CTA exits
             for (int i = max(0, issued - kSB); i < issued; ++i)
                 gwait(&bfull[i % kSB], (i / kSB) & 1, abort_flag, g.err, true, g.timeout_ns);
             for (int i = max(0, nch - kSB); i < nch; ++i)
@@ -267,8 +257,7 @@ fwd_gemm_kernel(const GemmArgs g) {
                         mma_ts(d_t, a_hi + kSPC + 8 * q, dh + q * kKStep, idesc, 1u);
                     }
                 }
-                if (C > 1) tc::mma_commit_mc(&bempty[s], cmask);
-                else tc::mma_commit(&bempty[s]);
+                tc::mma_commit(&bempty[s]);
                 tc::mma_commit(&aempty[sa]);
             }
             tc::mma_commit(&accfull);
@@ -307,10 +296,10 @@ fwd_gemm_kernel(const GemmArgs g) {
             }
         }
         // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) (SNRL, Eq. 38) while the first
-        // B stages are still in flight: FP32 products and partials, double-float tree
+        // B stages are still in flight: exact products, double-float partials and tree
         if (a.cdiag != nullptr && tile == 0 && ct == 0) {
             const bool diag = (m == l);
-            float sr = 0.f, si = 0.f;
+            DFloat sr = {0.f, 0.f}, si = {0.f, 0.f};
             if (diag) {
                 for (int n0 = r; n0 < N; n0 += kTM * FB) {
                     float2 xv[FB], hv[FB];
@@ -321,13 +310,10 @@ fwd_gemm_kernel(const GemmArgs g) {
                         hv[q] = n < N ? hl[n] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
-                    for (int q = 0; q < FB; ++q) {
-                        sr = fmaf(xv[q].x, hv[q].x, fmaf(xv[q].y, hv[q].y, sr));
-                        si = fmaf(xv[q].y, hv[q].x, fmaf(-xv[q].x, hv[q].y, si));
-                    }
+                    for (int q = 0; q < FB; ++q) df_acc_xconjh(xv[q], hv[q], sr, si);
                 }
             }
-            const DFloat dr = df_warp_sum({sr, 0.f}), di = df_warp_sum({si, 0.f});
+            const DFloat dr = df_warp_sum(sr), di = df_warp_sum(si);
             if (lane == 0) { red[t][0][warp & 3] = dr; red[t][1][warp & 3] = di; }
             asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
             if (diag && r == 0) {
@@ -460,8 +446,7 @@ fwd_gemm_kernel(const GemmArgs g) {
     }
 
     tc::fence_before_sync();
-    if (C > 1) tc::cluster_sync();   // no CTA leaves while the cluster still addresses it
-    else __syncthreads();
+    __syncthreads();
     if (warp == WMMA) {
         __syncwarp();
         tc::fence_after_sync();
@@ -503,15 +488,8 @@ static cudaError_t launch_cfg(const GemmArgs& g, int smem, cudaStream_t s, bool 
     cfg.blockDim = dim3(32 * (4 * T + 2));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     int na = 0;
-    if (g.csize > 1) {
-        at[na].id = cudaLaunchAttributeClusterDimension;
-        at[na].val.clusterDim.x = g.csize;
-        at[na].val.clusterDim.y = 1;
-        at[na].val.clusterDim.z = 1;
-        ++na;
-    }
     if (g.f.pdl) {
         at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[na].val.programmaticStreamSerializationAllowed = 1;
@@ -576,7 +554,6 @@ cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s) {
         return cudaErrorInvalidValue;
     const int P = g.f.M * g.f.M;
     if (!(g.tiles == 1 || g.tiles == 2) || P % g.tiles != 0) return cudaErrorInvalidValue;
-    if (!(g.csize == 1 || g.csize == 2 || g.csize == 4) || (P / g.tiles) % g.csize != 0) return cudaErrorInvalidValue;
     return dispatch(g, s, false);
 }
 

@@ -107,7 +107,6 @@ struct GemmArgs {
     int spc;                    // samples per pipeline stage
     int sb, sa;                 // stages of B images (shared memory) and of lag products (tensor memory)
     int tiles;                  // pairs (delay tiles) per CTA sharing each B stage (1, or 2 when M*M is even)
-    int csize;                  // CTAs per cluster sharing each B stage (1, 2 or 4; divides M*M / tiles)
     unsigned long long timeout_ns;  // limit of every pipeline wait
     int test_stall;             // failure-detection test: the MMA issuer waits on a barrier nothing completes
 };
@@ -116,6 +115,10 @@ int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles);
 bool gemm_shape_supported(int L, int N, int spc, int sb, int sa, int tiles);
 cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles);
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
+
+// Record the message of a failed call that has no context (read back by
+// af_last_error(NULL) on the same thread).
+void set_thread_error(const char* msg);
 
 struct QuantArgs;
 struct FinArgs;

@@ -28,6 +28,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "../../include/sqngd.h"
 #include "af_common.cuh"
 #include "af_kernels.h"
@@ -92,8 +94,16 @@ __global__ void fill_tables_kernel(float2* tw, float2* wL, float2* pre, PassTabl
     }
 }
 
-unsigned char* g_scratch_ptr[64];
-char g_error[256];   // reason of the last rejection, kept for debuggers
+unsigned char* g_scratch_ptr[64];   // device address of the array, per device (set once, under g_setup)
+std::mutex g_setup;
+
+// The calling thread's failure message (af_last_error(NULL)), then the status.
+af_status fail(af_status st, const char* fmt, const char* what) {
+    char b[320];
+    snprintf(b, sizeof b, fmt, what);
+    set_thread_error(b);
+    return st;
+}
 
 }  // namespace
 }  // namespace af
@@ -103,10 +113,7 @@ using namespace af;
 extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, double nu0, int32_t k_lo,
                                            int32_t k_hi, double eps, double snrl_db, const float* x_dev,
                                            const float* h_dev, double* terms_dev, void* stream) {
-    auto bad = [](const char* m) {
-        snprintf(g_error, sizeof g_error, "af_loss_terms_noalloc: %s", m);
-        return AF_ERR_INVALID_ARG;
-    };
+    auto bad = [](const char* m) { return fail(AF_ERR_INVALID_ARG, "af_loss_terms_noalloc: %s", m); };
     if (!x_dev || !h_dev || !terms_dev) return bad("x, h and terms must not be NULL");
     if (M < 1 || M > kMaxM) return bad("M must be in 1..16");
     if (N < 2 || N > kMaxN) return bad("N must be in 2..4096");
@@ -121,25 +128,23 @@ extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, doub
     // once per device: the array's device address
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
-        snprintf(g_error, sizeof g_error, "af_loss_terms_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
-        return AF_ERR_CUDA;
-    }
-    if (g_scratch_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            snprintf(g_error, sizeof g_error, "af_loss_terms_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            return AF_ERR_CUDA;
+    if (e != cudaSuccess) return fail(AF_ERR_CUDA, "af_loss_terms_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return fail(AF_ERR_CUDA, "af_loss_terms_noalloc: %s", "device ordinal above 63");
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup);
+        if (g_scratch_ptr[dev] == nullptr) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || p == nullptr)
+                return fail(AF_ERR_CUDA, "af_loss_terms_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_scratch_ptr[dev] = (unsigned char*)p;
         }
-        e = fft_prepare_f32(L, N, E);
-        if (e != cudaSuccess) {
-            snprintf(g_error, sizeof g_error, "af_loss_terms_noalloc: kernel attribute: %s", cudaGetErrorString(e));
-            return AF_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = (unsigned char*)p;
+        base = g_scratch_ptr[dev];
     }
-    unsigned char* base = g_scratch_ptr[dev];
+    // the shared-memory limit of this (L, E) instantiation (a no-op once raised)
+    e = fft_prepare_f32(L, N, E);
+    if (e != cudaSuccess) return fail(AF_ERR_CUDA, "af_loss_terms_noalloc: kernel attribute: %s", cudaGetErrorString(e));
     float2* tw = (float2*)(base + kOffTw);
     float2* wL = (float2*)(base + kOffWL);
     float2* pre = (float2*)(base + kOffPre);
@@ -188,9 +193,7 @@ extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, doub
         f.mode = FIN_GRAD_XH; f.terms = terms_dev;
         e = launch_fin(f, s);
     }
-    if (e != cudaSuccess) {
-        snprintf(g_error, sizeof g_error, "af_loss_terms_noalloc: launch: %s", cudaGetErrorString(e));
-        return AF_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return fail(AF_ERR_CUDA, "af_loss_terms_noalloc: launch: %s", cudaGetErrorString(e));
+    set_thread_error("");
     return AF_OK;
 }

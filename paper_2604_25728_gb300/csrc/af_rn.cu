@@ -558,6 +558,26 @@ extern "C" af_status rn_get_params(rn_net* n, float* theta_host) {
     return AF_OK;
 }
 
+extern "C" af_status rn_set_adam(rn_net* n, const float* m_host, const float* v_host) {
+    if (!n) return AF_ERR_INVALID_ARG;
+    if (!m_host || !v_host) RN_FAIL(n, AF_ERR_INVALID_ARG, "rn_set_adam: m and v must not be NULL");
+    const size_t T = (size_t)n->o.total;
+    RN_CK(n, cudaStreamSynchronize(n->stream));
+    RN_CK(n, cudaMemcpy(n->m, m_host, sizeof(float) * T, cudaMemcpyHostToDevice));
+    RN_CK(n, cudaMemcpy(n->v, v_host, sizeof(float) * T, cudaMemcpyHostToDevice));
+    return AF_OK;
+}
+
+extern "C" af_status rn_get_adam(rn_net* n, float* m_host, float* v_host) {
+    if (!n) return AF_ERR_INVALID_ARG;
+    if (!m_host || !v_host) RN_FAIL(n, AF_ERR_INVALID_ARG, "rn_get_adam: m and v must not be NULL");
+    const size_t T = (size_t)n->o.total;
+    RN_CK(n, cudaStreamSynchronize(n->stream));
+    RN_CK(n, cudaMemcpy(m_host, n->m, sizeof(float) * T, cudaMemcpyDeviceToHost));
+    RN_CK(n, cudaMemcpy(v_host, n->v, sizeof(float) * T, cudaMemcpyDeviceToHost));
+    return AF_OK;
+}
+
 extern "C" af_status rn_forward(rn_net* n, const float* y0_dev, float* u_dev) {
     if (!n) return AF_ERR_INVALID_ARG;
     if (!y0_dev || !u_dev) RN_FAIL(n, AF_ERR_INVALID_ARG, "rn_forward: y0 and u must not be NULL");

@@ -88,8 +88,8 @@ struct FinArgs {
     float* gy_out;            // [M][N] dL/dy and the z it was taken at (trainable thresholds), or null
     float* z_out;
     float* du_out;            // FIN_ADAM_U: [M][N] dL/du written instead of the Adam step (generator), or null
-    // FP32 copies of the double constants above, filled by launch_fin
-    float eps_f, ptar_f, inv_N_f, snrl_coef_f, inv_M_f, p_accept2_f;
+    // FP32 copy of eps (the sparse gradient coefficient), filled by launch_fin
+    float eps_f;
 };
 
 enum RhoMode : int {

@@ -121,7 +121,6 @@ struct af_ctx {
     int gemm_n_ct = 0, gemm_n_kc = 0;
     int gemm_spc = 32, gemm_sb = 2, gemm_sa = 2;   // samples per stage, B stages, A stages
     int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
-    int gemm_csize = 1;                   // CTAs per cluster sharing each B stage
     unsigned long long gemm_timeout_ns = 2000000000ull;   // limit of every pipeline wait
     int gemm_test_stall = 0;              // failure-detection test hook (SQNGD_GEMM_TEST_STALL)
     double2* pre64 = nullptr;
@@ -177,8 +176,11 @@ struct af_ctx {
     size_t g_log_cap = 0;
 };
 
-// messages of failures that have no context to hold them (af_init, af_last_error(NULL)), one per thread
+// messages of failures that have no context to hold them (af_init,
+// af_loss_terms_noalloc), one per thread; af_last_error(NULL) returns it
 static thread_local std::string g_init_error;
+
+void af::set_thread_error(const char* msg) { g_init_error = msg ? msg : ""; }
 
 #define FAIL(ctx, code, ...)                                        \
     do {                                                            \
@@ -355,14 +357,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         }
         const int P = M * M;
         c->gemm_tiles = 1;
-        c->gemm_csize = 1;
         if (const char* e = getenv("SQNGD_GEMM_TILES")) {
             const int v = atoi(e);
             if ((v == 1 || v == 2) && P % v == 0) c->gemm_tiles = v;
-        }
-        if (const char* e = getenv("SQNGD_GEMM_CLUSTER")) {
-            const int v = atoi(e);
-            if ((v == 1 || v == 2 || v == 4) && (P / c->gemm_tiles) % v == 0) c->gemm_csize = v;
         }
         // failure-detection test: every forward's MMA issuer waits on a barrier
         // that nothing completes, with a 50 ms limit
@@ -623,7 +620,6 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
         g.sb = c->gemm_sb;
         g.sa = c->gemm_sa;
         g.tiles = c->gemm_tiles;
-        g.csize = c->gemm_csize;
         g.timeout_ns = c->gemm_timeout_ns;
         g.test_stall = c->gemm_test_stall;
         return launch_fwd_gemm(g, s);
@@ -632,13 +628,14 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
 }
 
 // The forward pass of one evaluation, followed for the p-norm loss by the
-// dense adjoint (whose summed gradient the finish kernel then adds).
+// dense adjoint (whose summed gradient the finish kernel then adds) unless
+// no gradient is wanted (`adjoint` false: the loss terms alone).
 static cudaError_t launch_eval_forward(af_ctx* c, const float2* x, const float2* h, cudaStream_t s,
-                                       long long* ctr_inc) {
+                                       long long* ctr_inc, bool adjoint = true) {
     FwdArgs<float2, float> a = fwd_args(c, x, h);
     a.ctr_inc = ctr_inc;
     cudaError_t e = launch_fwd(c, a, s);
-    if (e != cudaSuccess || !(c->cfg.pnorm > 0.0)) return e;
+    if (e != cudaSuccess || !(c->cfg.pnorm > 0.0) || !adjoint) return e;
     AdjArgs d{};
     d.M = c->cfg.M; d.N = c->cfg.N; d.L = c->cfg.L; d.D = c->D; d.k_lo = c->cfg.k_lo;
     d.n_chunks = c->n_chunks; d.rows_per_chunk = c->rows_per_chunk;
@@ -734,8 +731,10 @@ extern "C" af_status af_loss_grad_xh(af_ctx* c, const float* x, const float* h, 
         h = x;
     }
     if (!x || !h) FAIL(c, AF_ERR_INVALID_ARG, "af_loss_grad_xh: x and h must not be NULL");
-    CK(c, launch_eval_forward(c, (const float2*)x, (const float2*)h, c->stream, nullptr));
+    const bool want = gx != nullptr || gh != nullptr;
+    CK(c, launch_eval_forward(c, (const float2*)x, (const float2*)h, c->stream, nullptr, want));
     FinArgs f = fin_args(c);
+    if (!want) { f.dense_g = nullptr; f.n_dense = 0; }
     f.mode = FIN_GRAD_XH;
     f.x = (const float2*)x;
     f.h_in = (const float2*)h;
@@ -756,8 +755,10 @@ extern "C" af_status af_loss_grad(af_ctx* c, const float* u, const float* h, int
     float2* x = use_hard ? c->xh : c->xs;
     if (c->cfg.matched) h = (const float*)x;
     CK(c, launch_wave_from_logits(u, MN, q, use_hard ? 1 : 0, x, c->dydz, nullptr, c->stream));
-    CK(c, launch_eval_forward(c, x, (const float2*)h, c->stream, nullptr));
+    const bool want = (gu != nullptr && !use_hard) || gh != nullptr;
+    CK(c, launch_eval_forward(c, x, (const float2*)h, c->stream, nullptr, want));
     FinArgs f = fin_args(c);
+    if (!want) { f.dense_g = nullptr; f.n_dense = 0; }
     f.mode = use_hard ? FIN_GRAD_XH : FIN_GRAD_U;
     f.x = x;
     f.dydz = c->dydz;
@@ -1022,6 +1023,93 @@ extern "C" af_status sqngd_step(af_ctx* c, af_state* st, int32_t n_outer, double
     st->t_x += (int64_t)n_outer * c->cfg.n_x;
     st->outer += n_outer;
     if (log_host) return af_sync(c);
+    return AF_OK;
+}
+
+// Algorithm 1's stopping test over sqngd_step (Section III-C).  After outer
+// iteration t the rule fires when t - best_outer >= patience; until an
+// improvement, it cannot fire before t = best_outer + patience, so the next
+// chunk runs exactly up to that iteration (or to t_max).  An improvement
+// inside a chunk moves the earliest firing point past the chunk's end.
+extern "C" af_status sqngd_run(af_ctx* c, af_state* st, int64_t t_max, int32_t patience, af_stop* stop,
+                               double* log_host, int64_t* n_done) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!st || !stop) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_run: st and stop must not be NULL");
+    if (patience < 1) FAIL(c, AF_ERR_INVALID_ARG, "sqngd_run: patience must be >= 1");
+    if (c->cfg.n_h < 1 && !c->cfg.matched)
+        FAIL(c, AF_ERR_INVALID_ARG, "sqngd_run: needs n_h >= 1 (or a matched context) to score the hard design");
+    const int ev = evals_per_outer(c);
+    const int64_t t0 = st->outer;
+    if (n_done) *n_done = 0;
+    stop->stopped = 0;
+    // a fresh record counts the patience from the first iteration of this run
+    if (stop->best_outer < 0) stop->best_outer = t0 - 1;
+    std::vector<double> buf;
+    while (st->outer < t_max) {
+        const int64_t t = st->outer;   // next outer iteration
+        const int64_t fire = stop->best_outer + patience;
+        int64_t chunk = fire - t + 1;
+        if (chunk < 1) chunk = 1;
+        if (chunk > t_max - t) chunk = t_max - t;
+        if (chunk > (1 << 20)) chunk = 1 << 20;
+        double* lg = nullptr;
+        if (log_host) lg = log_host + (size_t)(t - t0) * ev * 4;
+        else {
+            buf.resize((size_t)chunk * ev * 4);
+            lg = buf.data();
+        }
+        af_status s = sqngd_step(c, st, (int32_t)chunk, lg);
+        if (s != AF_OK) return s;
+        if (n_done) *n_done = st->outer - t0;
+        for (int64_t i = 0; i < chunk; ++i) {
+            const double w = lg[(size_t)i * ev * 4 + 1];   // L_WPSL of the iteration's first (hard) evaluation
+            if (w < stop->best_wpsl) { stop->best_wpsl = w; stop->best_outer = t + i; }
+            if (t + i - stop->best_outer >= patience) {
+                // the chunk was sized so that this is its last iteration
+                stop->stopped = 1;
+                return AF_OK;
+            }
+        }
+    }
+    stop->stopped = 2;
+    return AF_OK;
+}
+
+extern "C" af_status af_get_rho_state(af_ctx* c, float* rho_host, float* m_host, float* v_host, int32_t* uniform) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!rho_host) FAIL(c, AF_ERR_INVALID_ARG, "af_get_rho_state: rho is NULL");
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaStreamSynchronize(c->cap));
+    CK(c, cudaMemcpy(rho_host, c->rho, sizeof(float) * c->K, cudaMemcpyDeviceToHost));
+    for (float* dst : {m_host, v_host}) {
+        if (!dst) continue;
+        const float* src = (dst == m_host) ? c->m_rho : c->v_rho;
+        if (src) CK(c, cudaMemcpy(dst, src, sizeof(float) * c->K, cudaMemcpyDeviceToHost));
+        else memset(dst, 0, sizeof(float) * c->K);
+    }
+    if (uniform) *uniform = c->rho_uniform ? 1 : 0;
+    return AF_OK;
+}
+
+extern "C" af_status af_set_rho_state(af_ctx* c, const float* rho_host, const float* m_host, const float* v_host,
+                                      int32_t uniform) {
+    if (!c) return AF_ERR_INVALID_ARG;
+    if (!rho_host) FAIL(c, AF_ERR_INVALID_ARG, "af_set_rho_state: rho is NULL");
+    if (uniform != 0 && uniform != 1) FAIL(c, AF_ERR_INVALID_ARG, "af_set_rho_state: uniform must be 0 or 1");
+    if (uniform && c->cfg.train_rho) FAIL(c, AF_ERR_INVALID_ARG, "af_set_rho_state: trained thresholds read the table");
+    for (int i = 0; i < c->K; ++i) {
+        if (!(rho_host[i] >= 0.f && rho_host[i] <= 1.f)) FAIL(c, AF_ERR_INVALID_ARG, "rho[%d] outside [0, 1]", i);
+        if (i > 0 && !(rho_host[i] >= rho_host[i - 1])) FAIL(c, AF_ERR_INVALID_ARG, "rho decreases at %d", i);
+        if (uniform && rho_host[i] != (float)(((double)i + 0.5) / (double)c->K))
+            FAIL(c, AF_ERR_INVALID_ARG, "af_set_rho_state: uniform = 1 but rho[%d] is not the default threshold", i);
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaStreamSynchronize(c->cap));
+    CK(c, cudaMemcpy(c->rho, rho_host, sizeof(float) * c->K, cudaMemcpyHostToDevice));
+    if (c->m_rho && m_host) CK(c, cudaMemcpy(c->m_rho, m_host, sizeof(float) * c->K, cudaMemcpyHostToDevice));
+    if (c->v_rho && v_host) CK(c, cudaMemcpy(c->v_rho, v_host, sizeof(float) * c->K, cudaMemcpyHostToDevice));
+    c->rho_uniform = uniform != 0;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     return AF_OK;
 }
 

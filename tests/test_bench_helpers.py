@@ -94,3 +94,31 @@ def test_paper_fft_formulation_matches_the_oracle():
     r = orc.loss(x, h, nu, k_lo, k_hi)
     assert abs(float(wapsl) - r["wapsl"]) <= 1e-5 * r["wapsl"]
     assert abs(float(wcpsl) - r["wcpsl"]) <= 1e-5 * r["wcpsl"]
+
+
+def test_oracle_sample_share_by_enumeration():
+    """The reference sample (the delay window |k| <= 63 of the workload)
+    counts as its share of the lag products: enumerated pair by pair."""
+    w = wl.differentiation()
+    win = sum(w.N - abs(k) for k in range(-63, 64))
+    full = sum(w.N - abs(k) for k in range(w.k_lo, w.k_hi + 1))
+    assert full == w.N * w.N
+    assert abs(bench.sample_share(w) - win / full) < 1e-15
+    s = bench._oracle_window(w)
+    assert (s.k_lo, s.k_hi, s.M, s.N, s.L) == (-63, 63, w.M, w.N, w.L)
+
+
+def test_fp32_peak_from_unit_counts():
+    peak, note = bench._fp32_peak_tflops(sms=152, mhz=2070.0)
+    assert abs(peak - 152 * 128 * 2 * 2.070e9 / 1e12) < 1e-9 and "152 SMs" in note
+
+
+def test_adjoint_flops_by_enumeration():
+    """Per row of the winning class: two L-point transforms, 6 per cell (|chi|^2
+    and g) and 22 per valid lag product (the recomputed product and the two
+    gradient accumulations)."""
+    w = wl.small(2, 40, 4, 32, -10, 30)
+    valid = _valid_products(w)
+    rows = w.M * w.D
+    exp = rows * (2 * 5 * w.L * math.log2(w.L) + 6 * w.L) + 22 * valid * rows / w.D
+    assert abs(bench._adj_flops(w, rows) - exp) < 1e-9 * exp

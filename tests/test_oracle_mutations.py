@@ -47,6 +47,15 @@ MUTATIONS = [
     ("Eq. 42 weights swapped", "terms[0] = c->eps * lw + (1.0 - c->eps) * ls;",
      "terms[0] = (1.0 - c->eps) * lw + c->eps * ls;"),
     ("L_SNRL absolute instead of squared", "ls += (pm - ptar) * (pm - ptar);", "ls += fabs(pm - ptar);"),
+    ("sampled-cell decode with d and j swapped", "int j = (int)(id % L);\n        int d = (int)((id / L) % D);",
+     "int j = (int)((id / D) % L);\n        int d = (int)(id % D);"),
+    ("rank-one filter update without the conjugate", "? x[(size_t)m * N + n] * conj(delta) : 0.0;",
+     "? x[(size_t)m * N + n] * delta : 0.0;"),
+    ("rank-one waveform update at the wrong sample's phasor", "for (int j = 0; j < L; ++j) ej[j] = E[(size_t)j * N + n0];",
+     "for (int j = 0; j < L; ++j) ej[j] = E[(size_t)j * N];"),
+    ("rank-one update keeps the unperturbed peak of a touched pair",
+     "const fd_stat* s = touched ? &pert[((size_t)ci * 2 + side) * P + pair] : &base[pair];",
+     "const fd_stat* s = &base[pair];"),
     ("soft-quantizer derivative 1 - t", "ds += a * c * (1.0 - t * t);", "ds += a * c * (1.0 - t);"),
     ("thresholds i/K", "rho[i] = ((double)i + 0.5) / (double)K;", "rho[i] = (double)i / (double)K;"),
     ("Adam second moment of g, not g^2", "v[e] = b2 * v[e] + (1.0 - b2) * g[e] * g[e];",

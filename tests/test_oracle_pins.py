@@ -629,3 +629,94 @@ def test_acceptance_metrics_by_enumeration(orc):
     p = np.abs(np.sum(x * np.conj(h), axis=1)) / N
     np.testing.assert_allclose(snrl, -20 * np.log10(p), atol=1e-12)
     assert abs(out[3] - np.max(snrl)) < 1e-12
+
+
+# ------------------------------------------------ sampled cells, rank-one FD ----
+def test_ambiguity_cells_decode_on_a_non_square_grid(orc):
+    """The sampled-cell evaluator (the checker of every full-size GPU test)
+    decodes ((m M + l) D + d) L + j like the full grid: random cells of a grid
+    with D != L, a delay window that is not centred, an offset Doppler grid
+    and M = 3 (so a swapped m/l, d/j or D/L decode lands on another cell)."""
+    M, N, L, k_lo, k_hi = 3, 37, 11, -20, 8
+    nu = wl.full_grid(L) + 0.013
+    x, h = _random_pair(21, M, N)
+    ref = orc.ambiguity(x, h, nu, k_lo, k_hi).reshape(-1)
+    D = k_hi - k_lo + 1
+    assert D != L
+    cells = np.unique(np.concatenate([(wl.uniform(22, 400) * ref.size).astype(np.int64),
+                                      [0, ref.size - 1, L - 1, L, D * L - 1, D * L, M * D * L + 5]]))
+    got = orc.ambiguity_cells(x, h, nu, k_lo, k_hi, cells)
+    np.testing.assert_allclose(got, ref[cells], rtol=0, atol=1e-12)
+
+
+def _replaced(a, r, c, v):
+    b = a.copy()
+    b[r, c] = v
+    return b
+
+
+@pytest.mark.parametrize("pnorm", [0.0, 8.0])
+def test_fd_losses_equal_full_reevaluation(orc, pnorm):
+    """The rank-one finite-difference losses equal the loss re-evaluated in
+    full on explicitly perturbed inputs (x and h samples, both sides, samples
+    at the ends of a row, a non-centred delay window, a weight map and the
+    p-norm variant)."""
+    M, N, L, k_lo, k_hi = 3, 20, 16, -15, 9
+    nu = wl.full_grid(L) + 0.02
+    x, h = _random_pair(31, M, N)
+    D = k_hi - k_lo + 1
+    weights = 0.05 * (1.0 + wl.uniform(32, D * L).reshape(D, L))
+    weights[3, :4] = 0.0
+    coords = []
+    for i, (t, r, c) in enumerate([(0, 0, 0), (0, 2, 19), (1, 1, 7), (1, 0, 19), (0, 1, 10), (1, 2, 0)]):
+        base = (x if t == 0 else h)[r, c]
+        dv = 1e-3 * np.exp(1j * (0.7 + i))
+        coords.append((t, r, c, base + dv, base - dv))
+    for w in (None, weights):
+        lp, lm = orc.fd_losses(x, h, nu, k_lo, k_hi, coords, weights=w, eps=0.3, snrl_db=0.7, pnorm=pnorm)
+        for i, (t, r, c, vp, vm) in enumerate(coords):
+            for v, got in ((vp, lp[i]), (vm, lm[i])):
+                xx = _replaced(x, r, c, v) if t == 0 else x
+                hh = _replaced(h, r, c, v) if t == 1 else h
+                ref = orc.loss(xx, hh, nu, k_lo, k_hi, weights=w, eps=0.3, snrl_db=0.7, pnorm=pnorm)["loss"]
+                assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref)), (i, got, ref)
+
+
+def test_fd_losses_give_the_analytic_gradient(orc):
+    """Central differences of the rank-one losses reproduce the oracle's
+    analytic gradient (dL/dRe + j dL/dIm) at real and imaginary steps."""
+    M, N, L = 2, 24, 32
+    nu = wl.full_grid(L)
+    x, h = _random_pair(33, M, N)
+    _, gx, gh = orc.grad_xh(x, h, nu, -(N - 1), N - 1, eps=0.2, snrl_db=0.4, pnorm=6.0)
+    st = 1e-5
+    coords = []
+    picks = [(0, 0, 3), (0, 1, 17), (1, 0, 5), (1, 1, 23)]
+    for t, r, c in picks:
+        base = (x if t == 0 else h)[r, c]
+        coords += [(t, r, c, base + st, base - st), (t, r, c, base + 1j * st, base - 1j * st)]
+    lp, lm = orc.fd_losses(x, h, nu, -(N - 1), N - 1, coords, eps=0.2, snrl_db=0.4, pnorm=6.0)
+    fd = (lp - lm) / (2 * st)
+    for i, (t, r, c) in enumerate(picks):
+        g = (gx if t == 0 else gh)[r, c]
+        assert abs(fd[2 * i] - g.real) <= 1e-6 * np.abs(gx).max()
+        assert abs(fd[2 * i + 1] - g.imag) <= 1e-6 * np.abs(gx).max()
+
+
+# ------------------------------------------------------------- stopping rule ----
+def test_stop_rule_by_hand():
+    """Algorithm 1's stopping test on hand-made WPSL sequences: strict
+    improvement resets the count, equal values do not, the patience-th
+    iteration without improvement is the last one, T bounds the run, and a
+    resumed record continues the count."""
+    import oracle as orc
+    # best at t = 3 (3 < 4); t = 4, 5 bring nothing: stop after t = 5
+    assert orc.stop_rule([5, 4, 4, 3, 3, 3, 3, 1], 2, 100) == (6, 1, 3, 3)
+    # the first iteration always improves on a fresh record
+    assert orc.stop_rule([7.0] * 10, 3, 100) == (4, 1, 7.0, 0)
+    # T reached first
+    assert orc.stop_rule([9, 8, 7, 6, 5], 3, 4) == (4, 2, 6, 3)
+    # resumed at t0 = 10 with the best at iteration 8: the count continues (stop after t = 11)
+    assert orc.stop_rule([2.0, 2.0, 2.0], 3, 100, best_wpsl=1.5, best_outer=8, t0=10) == (2, 1, 1.5, 8)
+    # NaN never improves: a fresh record stops after `patience` iterations
+    assert orc.stop_rule([float("nan")] * 5, 2, 100)[:2] == (2, 1)

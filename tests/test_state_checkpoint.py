@@ -21,6 +21,7 @@ def _state(matched: bool, seed: int = 3):
     st.best_q.copy_(torch.from_numpy(wl.phase_indices(seed, M, N, 400)))
     st.best.copy_(torch.tensor([0.03125, 0.5, 17.0, 0.49], dtype=torch.float64))
     st.t_h, st.t_x, st.outer = 170, 160, 17
+    st.stop = [0.0412, 9]
     return st
 
 
@@ -31,6 +32,7 @@ def test_save_load_round_trip_is_bit_exact(tmp_path, matched):
     st.save(path)
     got = api.SqngdState.load(path, device="cpu")
     assert (got.t_h, got.t_x, got.outer) == (st.t_h, st.t_x, st.outer)
+    assert got.stop == st.stop
     for k in api.SqngdState._BUFFERS:
         a, b = getattr(st, k), getattr(got, k)
         if a is None:

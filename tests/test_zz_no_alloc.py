@@ -59,7 +59,11 @@ def test_noalloc_rejects_oversized_problems():
     x = torch.zeros((1, 16), dtype=torch.complex64, device="cuda")
     t = torch.zeros(9, dtype=torch.float64, device="cuda")
     p = ctypes.c_void_p
-    for M, N, L in ((17, 16, 32), (1, 5000, 32), (1, 16, 8192), (1, 16, 48)):
+    for M, N, L, why in ((17, 16, 32, "M must be in 1..16"), (1, 5000, 32, "N must be in 2..4096"),
+                         (1, 16, 8192, "L must be a power of two"), (1, 16, 48, "L must be a power of two")):
         st = lib.af_loss_terms_noalloc(M, N, L, ctypes.c_double(-0.5), 0, 1, ctypes.c_double(0.1),
                                        ctypes.c_double(0.5), p(x.data_ptr()), p(x.data_ptr()), p(t.data_ptr()), None)
         assert st == _lib.AF_ERR_INVALID_ARG
+        # the reason is readable on this thread through af_last_error(NULL)
+        msg = lib.af_last_error(None).decode()
+        assert msg.startswith("af_loss_terms_noalloc:") and why in msg, msg
