@@ -44,7 +44,7 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
 
 
 def test_committed_traffic_records_name_their_commands():
-    for name in ("fwd_fft_mid_traffic.json", "fwd_gemm_precision_traffic.json"):
+    for name in ("fwd_fft_mid_traffic.json", "fwd_gemm_precision_traffic.json", "fwd_fft_differentiation_traffic.json"):
         rec = json.load(open(os.path.join(ROOT, "profiles", name)))
         assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
         assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
