@@ -541,7 +541,7 @@ def run_ours(args):
                "sample": f"{evals} evaluations in {dt:.1f} s of FP64 CPU work on {_sample_note(w)}"}
 
     if rank == 0:
-        roof = {"bound": "alu", "kernel": "fwd_fft_kernel<2048,32> (af_forward)", "achieved": achieved,
+        roof = {"bound": "alu", "kernel": "fwd_fft_kernel<2048,32,512> (af_forward)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_note,
                 "algorithmic_flops_per_launch": flops, "launch_us": fwd_s * 1e6,
                 "launch_timing": f"{R} back-to-back af_forward launches between two CUDA events",

@@ -3,10 +3,11 @@
 // For every ordered pair (m, l) and delay k (Eq. 6, Eq. 34):
 //   chi_ml(k, nu_j) = sum_n x_m(n) conj(h_l(n+k)) e^{j 2 pi nu_0 n} e^{+j 2 pi j n / L}
 // i.e. an unnormalised inverse-sign L-point DFT of the lag products
-// (folded modulo L when N > L, zero-padded when N < L).  One CTA owns one
-// pair and a chunk of delays.  x_m (pre-modulated by e^{j 2 pi nu_0 n}, zero
-// beyond N) and h_l (with N zeros on each side) sit in shared memory, so each
-// row's products are formed in registers without bounds checks.  The row is
+// (folded modulo L when N > L, zero-padded when N < L).  One CTA of NT
+// threads owns one pair and a chunk of delays.  x_m (pre-modulated by
+// e^{j 2 pi nu_0 n}, zero beyond N) and the window of h_l that the chunk's
+// delays reach (zero outside [0, N)) sit in shared memory, so each row's
+// products are formed in registers without bounds checks.  The row is
 // transformed by a Stockham FFT with E values per thread (T = L/E threads per
 // row, radix E passes then the remainder, exchanges through a padded shared
 // buffer).  The last pass leaves chi in registers, where the sidelobe
@@ -20,13 +21,12 @@
 #include <stdlib.h>
 
 #include <type_traits>
+#include <vector>
 
 #include "af_common.cuh"
 #include "af_kernels.h"
 
 namespace af {
-
-constexpr int kThreads = 256;
 
 enum : int { MODE_REDUCE = 0, MODE_REDUCE_PNORM = 1, MODE_DUMP = 2 };
 
@@ -55,26 +55,39 @@ __device__ __forceinline__ void pnorm_merge(float hp, float& pv, float& ps, floa
 template <int L>
 __host__ __device__ constexpr int fold_len(int N) { return ((N + L - 1) / L) * L; }
 
-template <int L, int E, int MODE, typename C, typename K>
-__global__ void __launch_bounds__(kThreads)
+// Shared-memory entries of one CTA: x (XS), the h window (XS + rows per
+// chunk), the twiddles and RS padded row buffers.
+template <int L, int E, int NT>
+__host__ __device__ constexpr int fft_smem_entries(int N, int rpc) {
+    return fold_len<L>(N) * 2 + rpc + Plan<L, E>::tw_len + (NT / (L / E)) * Plan<L, E>::padlen;
+}
+
+// FP32 CTAs of 256 threads keep to 128 registers, so that two fit on an SM
+// when their shared memory allows.
+template <int L, int E, int NT, int MODE, typename C, typename K>
+__global__ void __launch_bounds__(NT, (NT == 256 && sizeof(C) == sizeof(float2)) ? 2 : 1)
 fwd_fft_kernel(const FwdArgs<C, K> a) {
     using PL = Plan<L, E>;
     using T = decltype(C{}.x);
+    constexpr int kThreads = NT;
     constexpr int TPR = PL::T;               // threads per row
     constexpr int RS = kThreads / TPR;       // row slots per CTA
     constexpr int RL = PL::radix(PL::passes - 1), NSL = PL::ns(PL::passes - 1), NBL = E / RL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N;
     const int XS = fold_len<L>(N);
+    const int HS = XS + a.rows_per_chunk;     // h window of this CTA's delays
     C* xs = reinterpret_cast<C*>(smem_raw);   // [XS]
-    C* hp = xs + XS;                          // [2N + XS], h_l(p) at hp[N + p]
-    C* tws = hp + 2 * N + XS;                 // [tw_len]
+    C* hs = xs + XS;                          // [HS], h_l(k_first + i) at hs[i]
+    C* tws = hs + HS;                         // [tw_len]
     C* bufs = tws + PL::tw_len;               // [RS][padlen]
 
     const int tid = threadIdx.x;
     const int pair = blockIdx.x / a.n_chunks;
     const int chunk = blockIdx.x - pair * a.n_chunks;
     const int m = pair / a.M, l = pair - m * a.M;
+    const int d_begin = chunk * a.rows_per_chunk;
+    const int k_first = a.k_lo + d_begin;     // smallest delay of the chunk
 
     // Constant tables first: with programmatic launch this overlaps the tail
     // of the kernel that produces x and h.
@@ -103,18 +116,20 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                 if (n < XS) xs[n] = cmul(xv[q], pv[q]);
             }
         }
-        for (int i0 = tid; i0 < 2 * N + XS; i0 += kThreads * FB) {
+        // row k reads h_l(n + k) for n < XS: with k_first <= k < k_first +
+        // rows_per_chunk that is hs[0 .. XS + rows_per_chunk - 1)
+        for (int i0 = tid; i0 < HS; i0 += kThreads * FB) {
             C hv[FB];
 #pragma unroll
             for (int q = 0; q < FB; ++q) {
                 const int i = i0 + q * kThreads;
-                const int p = i - N;
-                hv[q] = (p >= 0 && p < N && i < 2 * N + XS) ? hl[p] : zero;
+                const int p = k_first + i;
+                hv[q] = (p >= 0 && p < N && i < HS) ? hl[p] : zero;
             }
 #pragma unroll
             for (int q = 0; q < FB; ++q) {
                 const int i = i0 + q * kThreads;
-                if (i < 2 * N + XS) hp[i] = hv[q];
+                if (i < HS) hs[i] = hv[q];
             }
         }
     }
@@ -150,7 +165,6 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     const int slot = tid / TPR;
     const int t = tid - slot * TPR;
     C* buf = bufs + slot * PL::padlen;
-    const int d_begin = chunk * a.rows_per_chunk;
     const int d_end = min(a.D, d_begin + a.rows_per_chunk);
     const int NF = XS / L;
     const bool auto_pair = (m == l);
@@ -163,11 +177,11 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     for (int d0 = d_begin; d0 < d_end; d0 += RS) {
         const int d = d0 + slot;
         const bool row_in = d < d_end;
-        const int k = row_in ? a.k_lo + d : 0;
+        const int k = row_in ? a.k_lo + d : k_first;   // rows past the chunk compute on valid data, unused
         // ---- pass 0: lag products (folded mod L) + radix-E butterflies ----
         C v[E];
         const C* xk = xs + t;
-        const C* hk = hp + N + k + t;
+        const C* hk = hs + (k - k_first) + t;
         if (NF == 1) {
 #pragma unroll
             for (int r = 0; r < E; ++r) v[r] = cmulc(xk[r * TPR], hk[r * TPR]);
@@ -263,175 +277,154 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
 }
 
 // ------------------------------------------------------------------ host ----
-// A row needs L/E <= 256 threads (one CTA), so L = 4096 takes E = 16 or 32.
-// E = 32 (one shared-memory exchange fewer, more registers) exists for the
-// FP32 forward pass only.
-static bool elems_ok(int L, int E) { return (E == 8 || E == 16 || E == 32) && L >= 2 * E && L / E <= kThreads; }
-
-template <int L, int E, typename C>
-static int smem_for(int N) {
-    using PL = Plan<L, E>;
-    const int XS = fold_len<L>(N);
-    return (int)sizeof(C) * (XS + 2 * N + XS + PL::tw_len + (kThreads / PL::T) * PL::padlen);
+// A row needs L/E <= NT threads (one CTA).  E = 32 (one shared-memory
+// exchange fewer, more registers) exists for the FP32 forward pass only; CTAs
+// of 512 threads (twice the rows per CTA, sharing x, h and the twiddles) for
+// FP32 rows of 1024 bins and more.
+static bool shape_ok(int L, int E, int NT, bool fp64) {
+    if (!(E == 8 || E == 16 || E == 32) || L < 2 * E || L / E > NT) return false;
+    if (fp64) return E != 32 && NT == 256;
+    return NT == 256 || (NT == 512 && E >= 16 && L >= 1024);
 }
 
-template <int L, int E, int MODE, typename C, typename K>
+template <int L, int E, int NT, typename C>
+static int smem_for(int N, int rpc) {
+    return (int)sizeof(C) * fft_smem_entries<L, E, NT>(N, rpc);
+}
+
+template <int L, int E, int NT, int MODE, typename C, typename K>
 static cudaError_t launch_LEM(const FwdArgs<C, K>& a, cudaStream_t s, bool prepare_only) {
-    const int smem = smem_for<L, E, C>(a.N);
-    auto kern = fwd_fft_kernel<L, E, MODE, C, K>;
+    const int smem = smem_for<L, E, NT, C>(a.N, a.rows_per_chunk);
+    auto kern = fwd_fft_kernel<L, E, NT, MODE, C, K>;
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess || prepare_only) return e;
     const int grid = a.M * a.M * a.n_chunks;
-    return launch_ex(kern, dim3(grid), dim3(kThreads), smem, s, a.pdl != 0, a);
+    return launch_ex(kern, dim3(grid), dim3(NT), smem, s, a.pdl != 0, a);
 }
 
-template <int L, int E, typename C, typename K>
+template <int L, int E, int NT, typename C, typename K>
 static cudaError_t launch_LE(const FwdArgs<C, K>& a, cudaStream_t s, bool prepare_only) {
     if constexpr (sizeof(C) == sizeof(double2)) {
         // FP64 acceptance pass: exact max only
-        return launch_LEM<L, E, MODE_REDUCE, C, K>(a, s, prepare_only);
+        return launch_LEM<L, E, NT, MODE_REDUCE, C, K>(a, s, prepare_only);
     } else {
         if (prepare_only) {
-            cudaError_t e = launch_LEM<L, E, MODE_REDUCE, C, K>(a, s, true);
-            if (e == cudaSuccess) e = launch_LEM<L, E, MODE_REDUCE_PNORM, C, K>(a, s, true);
-            if (e == cudaSuccess) e = launch_LEM<L, E, MODE_DUMP, C, K>(a, s, true);
+            cudaError_t e = launch_LEM<L, E, NT, MODE_REDUCE, C, K>(a, s, true);
+            if (e == cudaSuccess) e = launch_LEM<L, E, NT, MODE_REDUCE_PNORM, C, K>(a, s, true);
+            if (e == cudaSuccess) e = launch_LEM<L, E, NT, MODE_DUMP, C, K>(a, s, true);
             return e;
         }
-        if (a.mode == FWD_DUMP) return launch_LEM<L, E, MODE_DUMP, C, K>(a, s, false);
-        if (a.half_p > 0.f) return launch_LEM<L, E, MODE_REDUCE_PNORM, C, K>(a, s, false);
-        return launch_LEM<L, E, MODE_REDUCE, C, K>(a, s, false);
+        if (a.mode == FWD_DUMP) return launch_LEM<L, E, NT, MODE_DUMP, C, K>(a, s, false);
+        if (a.half_p > 0.f) return launch_LEM<L, E, NT, MODE_REDUCE_PNORM, C, K>(a, s, false);
+        return launch_LEM<L, E, NT, MODE_REDUCE, C, K>(a, s, false);
     }
 }
 
+// Every built (L, E, NT) instantiation, in one table: X(L, E, NT).
+#define AF_FFT_F32_SHAPES(X)                                                                                 \
+    X(32, 8, 256) X(32, 16, 256) X(64, 8, 256) X(64, 16, 256) X(64, 32, 256) X(128, 8, 256) X(128, 16, 256) \
+    X(128, 32, 256) X(256, 8, 256) X(256, 16, 256) X(256, 32, 256) X(512, 8, 256) X(512, 16, 256)           \
+    X(512, 32, 256) X(1024, 8, 256) X(1024, 16, 256) X(1024, 32, 256) X(2048, 8, 256) X(2048, 16, 256)      \
+    X(2048, 32, 256) X(4096, 16, 256) X(4096, 32, 256) X(1024, 16, 512) X(1024, 32, 512) X(2048, 16, 512)    \
+    X(2048, 32, 512) X(4096, 16, 512) X(4096, 32, 512)
+#define AF_FFT_F64_SHAPES(X)                                                                                 \
+    X(32, 8, 256) X(32, 16, 256) X(64, 8, 256) X(64, 16, 256) X(128, 8, 256) X(128, 16, 256) X(256, 8, 256)  \
+    X(256, 16, 256) X(512, 8, 256) X(512, 16, 256) X(1024, 8, 256) X(1024, 16, 256) X(2048, 8, 256)         \
+    X(2048, 16, 256) X(4096, 16, 256)
+
 template <typename C, typename K>
 static cudaError_t launch_any(const FwdArgs<C, K>& a, cudaStream_t s, bool prepare_only) {
+    const int NT = a.fft_nt ? a.fft_nt : 256;
+#define AF_FFT_CASE(LL, EE, TT) \
+    if (a.L == LL && a.fft_e == EE && NT == TT) return launch_LE<LL, EE, TT>(a, s, prepare_only);
     if constexpr (sizeof(C) == sizeof(float2)) {
-        if (a.fft_e == 32) {
-            switch (a.L) {
-                case 64: return launch_LE<64, 32>(a, s, prepare_only);
-                case 128: return launch_LE<128, 32>(a, s, prepare_only);
-                case 256: return launch_LE<256, 32>(a, s, prepare_only);
-                case 512: return launch_LE<512, 32>(a, s, prepare_only);
-                case 1024: return launch_LE<1024, 32>(a, s, prepare_only);
-                case 2048: return launch_LE<2048, 32>(a, s, prepare_only);
-                case 4096: return launch_LE<4096, 32>(a, s, prepare_only);
-                default: return cudaErrorInvalidValue;
-            }
-        }
+        AF_FFT_F32_SHAPES(AF_FFT_CASE)
     } else {
-        if (a.fft_e == 32) return cudaErrorInvalidValue;
+        AF_FFT_F64_SHAPES(AF_FFT_CASE)
     }
-    const bool e8 = (a.fft_e == 8);
-    switch (a.L) {
-        case 32: return e8 ? launch_LE<32, 8>(a, s, prepare_only) : launch_LE<32, 16>(a, s, prepare_only);
-        case 64: return e8 ? launch_LE<64, 8>(a, s, prepare_only) : launch_LE<64, 16>(a, s, prepare_only);
-        case 128: return e8 ? launch_LE<128, 8>(a, s, prepare_only) : launch_LE<128, 16>(a, s, prepare_only);
-        case 256: return e8 ? launch_LE<256, 8>(a, s, prepare_only) : launch_LE<256, 16>(a, s, prepare_only);
-        case 512: return e8 ? launch_LE<512, 8>(a, s, prepare_only) : launch_LE<512, 16>(a, s, prepare_only);
-        case 1024: return e8 ? launch_LE<1024, 8>(a, s, prepare_only) : launch_LE<1024, 16>(a, s, prepare_only);
-        case 2048: return e8 ? launch_LE<2048, 8>(a, s, prepare_only) : launch_LE<2048, 16>(a, s, prepare_only);
-        case 4096: return e8 ? cudaErrorInvalidValue : launch_LE<4096, 16>(a, s, prepare_only);
-        default: return cudaErrorInvalidValue;
-    }
+#undef AF_FFT_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s) { return launch_any(a, s, false); }
 cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s) { return launch_any(a, s, false); }
 
-template <int L, int E, typename C, typename K>
-static int occupancy_LE(int N) {
+template <int L, int E, int NT, typename C, typename K>
+static int occupancy_LE(int N, int rpc) {
+    // the occupancy query counts a launch above the kernel's shared-memory
+    // limit as impossible, so the limit is raised first
+    auto kern = fwd_fft_kernel<L, E, NT, MODE_REDUCE, C, K>;
+    const int smem = smem_for<L, E, NT, C>(N, rpc);
+    if (smem > 227 * 1024 || set_smem_once(reinterpret_cast<const void*>(kern), smem) != cudaSuccess) return 1;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd_fft_kernel<L, E, MODE_REDUCE, C, K>, kThreads,
-                                                      smem_for<L, E, C>(N)) != cudaSuccess)
-        return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem) != cudaSuccess) return 1;
     return occ > 0 ? occ : 1;
 }
 
-template <typename C, typename K>
-static int occupancy_any(int L, int N, int E) {
-    if constexpr (sizeof(C) == sizeof(float2)) {
-        if (E == 32) {
-            switch (L) {
-                case 64: return occupancy_LE<64, 32, C, K>(N);
-                case 128: return occupancy_LE<128, 32, C, K>(N);
-                case 256: return occupancy_LE<256, 32, C, K>(N);
-                case 512: return occupancy_LE<512, 32, C, K>(N);
-                case 1024: return occupancy_LE<1024, 32, C, K>(N);
-                case 2048: return occupancy_LE<2048, 32, C, K>(N);
-                case 4096: return occupancy_LE<4096, 32, C, K>(N);
-                default: return 1;
-            }
-        }
-    }
-    const bool e8 = (E == 8);
-    switch (L) {
-        case 32: return e8 ? occupancy_LE<32, 8, C, K>(N) : occupancy_LE<32, 16, C, K>(N);
-        case 64: return e8 ? occupancy_LE<64, 8, C, K>(N) : occupancy_LE<64, 16, C, K>(N);
-        case 128: return e8 ? occupancy_LE<128, 8, C, K>(N) : occupancy_LE<128, 16, C, K>(N);
-        case 256: return e8 ? occupancy_LE<256, 8, C, K>(N) : occupancy_LE<256, 16, C, K>(N);
-        case 512: return e8 ? occupancy_LE<512, 8, C, K>(N) : occupancy_LE<512, 16, C, K>(N);
-        case 1024: return e8 ? occupancy_LE<1024, 8, C, K>(N) : occupancy_LE<1024, 16, C, K>(N);
-        case 2048: return e8 ? occupancy_LE<2048, 8, C, K>(N) : occupancy_LE<2048, 16, C, K>(N);
-        case 4096: return occupancy_LE<4096, 16, C, K>(N);
-        default: return 1;
-    }
+int fft_occupancy(int L, int N, int E, bool fp64, int NT, int rpc) {
+#define AF_FFT_OCC32(LL, EE, TT) \
+    if (!fp64 && L == LL && E == EE && NT == TT) return occupancy_LE<LL, EE, TT, float2, float>(N, rpc);
+#define AF_FFT_OCC64(LL, EE, TT) \
+    if (fp64 && L == LL && E == EE && NT == TT) return occupancy_LE<LL, EE, TT, double2, double>(N, rpc);
+    AF_FFT_F32_SHAPES(AF_FFT_OCC32)
+    AF_FFT_F64_SHAPES(AF_FFT_OCC64)
+#undef AF_FFT_OCC32
+#undef AF_FFT_OCC64
+    return 1;
 }
 
-int fft_occupancy(int L, int N, int E, bool fp64) {
-    return fp64 ? occupancy_any<double2, double>(L, N, E) : occupancy_any<float2, float>(L, N, E);
-}
-
-cudaError_t fft_prepare_f32(int L, int N, int E) {
+cudaError_t fft_prepare_f32(int L, int N, int E, int NT, int rpc) {
     FwdArgs<float2, float> a{};
-    a.L = L; a.N = N; a.fft_e = E;
+    a.L = L; a.N = N; a.fft_e = E; a.fft_nt = NT; a.rows_per_chunk = rpc;
     return launch_any(a, nullptr, true);
 }
-cudaError_t fft_prepare_f64(int L, int N, int E) {
+cudaError_t fft_prepare_f64(int L, int N, int E, int NT, int rpc) {
     FwdArgs<double2, double> a{};
-    a.L = L; a.N = N; a.fft_e = E;
+    a.L = L; a.N = N; a.fft_e = E; a.fft_nt = NT; a.rows_per_chunk = rpc;
     return launch_any(a, nullptr, true);
 }
 
-template <int L, int E, typename C>
-static int smem_if(int N) {
-    if constexpr (L >= 2 * E && L / E <= kThreads) return smem_for<L, E, C>(N);
-    else return -1;
-}
+int fft_rows_per_cta(int L, int E, int NT) { return (E > 0 && L % E == 0 && L / E <= NT) ? NT / (L / E) : 0; }
 
-template <typename C, int E>
-static int smem_any(int L, int N) {
-    if (!elems_ok(L, E)) return -1;
-    switch (L) {
-        case 32: return smem_if<32, E, C>(N);
-        case 64: return smem_if<64, E, C>(N);
-        case 128: return smem_if<128, E, C>(N);
-        case 256: return smem_if<256, E, C>(N);
-        case 512: return smem_if<512, E, C>(N);
-        case 1024: return smem_if<1024, E, C>(N);
-        case 2048: return smem_if<2048, E, C>(N);
-        case 4096: return smem_if<4096, E, C>(N);
-        default: return -1;
+int fft_smem_bytes(int L, int N, bool fp64, int E, int NT, int rpc) {
+    if (!shape_ok(L, E, NT, fp64) || (L & (L - 1)) != 0 || L > 4096) return -1;
+    if (rpc <= 0) rpc = fft_rows_per_cta(L, E, NT);
+    const int XS = ((N + L - 1) / L) * L;
+    // the entries of fft_smem_entries, with the plan's table sizes
+    int tw = 0, ns = 1, rem = L;
+    std::vector<int> radices;
+    while (rem >= E && rem % E == 0) { radices.push_back(E); rem /= E; }
+    if (rem > 1) radices.push_back(rem);
+    for (size_t p = 0; p < radices.size(); ++p) {
+        if (p >= 1) tw += (radices[p] - 1) * ns;
+        ns *= radices[p];
     }
+    const long long entries = 2LL * XS + rpc + tw + (long long)(NT / (L / E)) * (L + L / E);
+    const long long bytes = entries * (fp64 ? (long long)sizeof(double2) : (long long)sizeof(float2));
+    return bytes > (1LL << 30) ? -1 : (int)bytes;
 }
-
-int fft_smem_bytes(int L, int N, bool fp64, int E) {
-    if (E == 32) return fp64 ? -1 : smem_any<float2, 32>(L, N);
-    if (E == 8) return fp64 ? smem_any<double2, 8>(L, N) : smem_any<float2, 8>(L, N);
-    return fp64 ? smem_any<double2, 16>(L, N) : smem_any<float2, 16>(L, N);
-}
-
-int fft_rows_per_cta(int L, int E) { return elems_ok(L, E) ? kThreads / (L / E) : 0; }
 
 int fft_default_elems(int L, bool fp64) {
     if (const char* e = getenv("SQNGD_FFT_E")) {
         const int v = atoi(e);
-        if (elems_ok(L, v) && !(fp64 && v == 32)) return v;
+        if (shape_ok(L, v, 256, fp64)) return v;
     }
-    if (fp64) return elems_ok(L, 8) ? 8 : 16;
+    if (fp64) return shape_ok(L, 8, 256, true) ? 8 : 16;
     // rows of 512 bins and more: 32 values per thread save one shared-memory
     // exchange per row (measured 4-6% faster at L = 512 and 2048; slower for
     // short rows, where fewer CTAs fit)
-    return (L >= 512 && elems_ok(L, 32)) ? 32 : 16;
+    return (L >= 512 && shape_ok(L, 32, 256, false)) ? 32 : 16;
+}
+
+int fft_default_threads(int L, int E, bool fp64) {
+    if (const char* e = getenv("SQNGD_FFT_NT")) {
+        const int v = atoi(e);
+        if (shape_ok(L, E, v, fp64)) return v;
+    }
+    // rows of 1024 bins and more with 32 values per thread: 512-thread CTAs
+    // hold 16 warps per SM where the shared memory of 256-thread CTAs allows
+    // one (measured at M=4, N=2048, L=2048: 326 -> 253 us per launch)
+    return shape_ok(L, E, 512, fp64) && E == 32 ? 512 : 256;
 }
 
 }  // namespace af

@@ -41,7 +41,8 @@ struct FwdArgs {
     double2* cdiag;        // [M] chi_mm(0,0) = sum_n x_m conj(h_m), FP64 (may be nullptr)
     C* chi_out;            // FWD_DUMP output
     long long* ctr_inc;    // if set, CTA 0 adds 1 to ctr_inc[0] (outer-iteration counter)
-    int fft_e;             // FFT path: values per thread (8 or 16); selects the twiddle plan
+    int fft_e;             // FFT path: values per thread (8, 16 or 32); selects the twiddle plan
+    int fft_nt;            // FFT path: threads per CTA (256, or 512 for FP32 rows of >= 1024 bins); 0 = 256
     C* pchi;               // [grid] chi at each CTA's best cell (may be nullptr)
     int pdl;               // launch with programmatic stream serialisation
 };
@@ -74,14 +75,17 @@ int adj_smem_bytes(int L, int N, int E);
 
 // FFT path with E values per thread: dynamic shared memory bytes (-1 if L
 // unsupported), row slots per 256-thread CTA, and the default E for L.
-int fft_smem_bytes(int L, int N, bool fp64, int E);
-int fft_rows_per_cta(int L, int E);
+// Shared memory of one forward CTA of NT threads whose delay chunk holds rpc
+// rows (rpc <= 0: one row per slot); -1 if the shape is not built.
+int fft_smem_bytes(int L, int N, bool fp64, int E, int NT = 256, int rpc = 0);
+int fft_rows_per_cta(int L, int E, int NT = 256);
 int fft_default_elems(int L, bool fp64);
-int fft_occupancy(int L, int N, int E, bool fp64);   // resident CTAs per SM (reduce kernel)
+int fft_default_threads(int L, int E, bool fp64);
+int fft_occupancy(int L, int N, int E, bool fp64, int NT, int rpc);   // resident CTAs per SM (reduce kernel)
 cudaError_t launch_fwd_fft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
 cudaError_t launch_fwd_fft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
-cudaError_t fft_prepare_f32(int L, int N, int E);
-cudaError_t fft_prepare_f64(int L, int N, int E);
+cudaError_t fft_prepare_f32(int L, int N, int E, int NT, int rpc);
+cudaError_t fft_prepare_f64(int L, int N, int E, int NT, int rpc);
 
 // Raise the dynamic shared-memory limit of the DFT kernels a context will use.
 cudaError_t dft_prepare_f32(int N);

@@ -121,7 +121,15 @@ extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, doub
     if (k_lo < -(N - 1) || k_hi > N - 1 || k_lo > k_hi) return bad("delay window outside [-(N-1), N-1]");
     if (!(eps >= 0.0 && eps <= 1.0) || !(snrl_db >= 0.0) || !isfinite(nu0)) return bad("bad eps, snrl_db or nu0");
     const int E = fft_default_elems(L, false);
-    const int smem = fft_smem_bytes(L, N, false, E);
+    // geometry: at most 32 delay chunks per pair
+    const int D = k_hi - k_lo + 1;
+    const int RS = fft_rows_per_cta(L, E);
+    int rows = (D + 31) / 32;
+    rows = ((rows + RS - 1) / RS) * RS;
+    const int n_chunks = (D + rows - 1) / rows;
+    const int nblk = M * M * n_chunks;
+    if (nblk > kMaxCtas) return bad("too many forward CTAs for the scratch array");
+    const int smem = fft_smem_bytes(L, N, false, E, 256, rows);
     if (smem <= 0 || smem > 227 * 1024) return bad("the forward pass does not fit in shared memory for this N, L");
     cudaStream_t s = (cudaStream_t)stream;
 
@@ -143,7 +151,7 @@ extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, doub
         base = g_scratch_ptr[dev];
     }
     // the shared-memory limit of this (L, E) instantiation (a no-op once raised)
-    e = fft_prepare_f32(L, N, E);
+    e = fft_prepare_f32(L, N, E, 256, rows);
     if (e != cudaSuccess) return fail(AF_ERR_CUDA, "af_loss_terms_noalloc: kernel attribute: %s", cudaGetErrorString(e));
     float2* tw = (float2*)(base + kOffTw);
     float2* wL = (float2*)(base + kOffWL);
@@ -160,15 +168,6 @@ extern "C" af_status af_loss_terms_noalloc(int32_t M, int32_t N, int32_t L, doub
         while (rem >= E && rem % E == 0 && pt.n < kMaxPasses) { pt.R[pt.n] = E; pt.NS[pt.n] = ns; ++pt.n; ns *= E; rem /= E; }
         if (rem > 1) { pt.R[pt.n] = rem; pt.NS[pt.n] = ns; ++pt.n; }
     }
-    // geometry: at most 32 delay chunks per pair
-    const int D = k_hi - k_lo + 1;
-    const int RS = fft_rows_per_cta(L, E);
-    int rows = (D + 31) / 32;
-    rows = ((rows + RS - 1) / RS) * RS;
-    const int n_chunks = (D + rows - 1) / rows;
-    const int nblk = M * M * n_chunks;
-    if (nblk > kMaxCtas) return bad("too many forward CTAs for the scratch array");
-
     fill_tables_kernel<<<32, 256, 0, s>>>(tw, wL, pre, pt, L, N, nu0);
     e = cudaGetLastError();
     if (e == cudaSuccess) {

@@ -137,6 +137,7 @@ struct af_ctx {
     bool rho_uniform = true;   // thresholds are the default (i + 1/2)/K
     bool pdl = true;           // programmatic dependent launch between forward and finish kernels
     int fft_e = 0, acc_e = 0;  // FFT values per thread: FP32 path, FP64 acceptance
+    int fft_nt = 256;          // threads per forward CTA (FP32 FFT path)
     int acc_n_chunks = 0, acc_rows_per_chunk = 0, acc_nblk = 0, acc_ctas_per_pair = 0;
     float* pkey = nullptr;
     long long* pidx = nullptr;
@@ -249,12 +250,16 @@ static void free_all(af_ctx* c) {
 // once.  Choose the iteration count per CTA that minimises
 // waves x (iterations + 1/2), the half iteration standing for the CTA's
 // prologue (loading x, h and the twiddles).
-static int pick_row_iters(int P, int D, int RS, int slots) {
-    if (slots < 1) slots = 1;
+// slots_of(it): resident CTAs on the whole GPU when a CTA's chunk holds it x RS
+// rows (its shared memory grows with the chunk's h window).
+template <typename SlotsOf>
+static int pick_row_iters(int P, int D, int RS, SlotsOf slots_of) {
     int best_it = 1;
     double best_cost = 1e300;
     const int max_it = (D + RS - 1) / RS;
     for (int it = 1; it <= max_it; ++it) {
+        int slots = slots_of(it);
+        if (slots < 1) slots = 1;
         const long long rows = (long long)it * RS;
         const long long ctas = (long long)P * ((D + rows - 1) / rows);
         const long long waves = (ctas + slots - 1) / slots;
@@ -339,7 +344,12 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     // the dense adjoint of the p-norm loss shares the forward's twiddle
     // tables and is built for 8 and 16 values per thread
     if (cfg->pnorm > 0.0 && c->fft_e == 32) c->fft_e = 16;
-    const int fft_smem = uniform ? fft_smem_bytes(L, N, false, c->fft_e) : -1;
+    c->fft_nt = uniform ? fft_default_threads(L, c->fft_e, false) : 256;
+    if (uniform && c->fft_nt != 256) {
+        const int wide = fft_smem_bytes(L, N, false, c->fft_e, c->fft_nt);
+        if (wide <= 0 || wide > 227 * 1024) c->fft_nt = 256;   // the wide CTA does not fit: 256 threads
+    }
+    const int fft_smem = uniform ? fft_smem_bytes(L, N, false, c->fft_e, c->fft_nt) : -1;
     uniform = uniform && fft_smem > 0 && fft_smem <= 227 * 1024;
     if (cfg->path == AF_PATH_FFT && !uniform) {
         c->err = "AF_PATH_FFT needs nu_j = nu_0 + j/L with L a power of two in 32..4096";
@@ -464,23 +474,14 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         if ((s = upload(c, &c->rho, rho))) return fail(s);
     }
 
-    // kernels' shared-memory limits are raised here, outside any graph capture
-    {
-        cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e)
-                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)
-                        : dft_prepare_f32(N);
-        if (e == cudaSuccess) e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e) : dft_prepare_f64(N);
-        if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
-        if (e == cudaSuccess && c->K <= 8192) e = rho_prepare(c->K);
-        if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
-    }
-
     // ---- launch geometry and workspace ----
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1) sms = 1;
     if (c->path == AF_PATH_FFT) {
-        const int RS = fft_rows_per_cta(L, c->fft_e);
-        int it = pick_row_iters(c->P, c->D, RS, sms * fft_occupancy(L, N, c->fft_e, false));
+        const int RS = fft_rows_per_cta(L, c->fft_e, c->fft_nt);
+        int it = pick_row_iters(c->P, c->D, RS, [&](int i) {
+            return sms * fft_occupancy(L, N, c->fft_e, false, c->fft_nt, i * RS);
+        });
         if (const char* e = getenv("SQNGD_FFT_ROW_ITERS")) it = atoi(e) > 0 ? atoi(e) : it;
         c->rows_per_chunk = RS * it;
         c->n_chunks = (c->D + c->rows_per_chunk - 1) / c->rows_per_chunk;
@@ -497,7 +498,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     c->nblk = c->P * c->ctas_per_pair;
     if (c->acc_fft) {
         const int RS = fft_rows_per_cta(L, c->acc_e);
-        const int it = pick_row_iters(c->P, c->D, RS, sms * fft_occupancy(L, N, c->acc_e, true));
+        const int it = pick_row_iters(c->P, c->D, RS, [&](int i) {
+            return sms * fft_occupancy(L, N, c->acc_e, true, 256, i * RS);
+        });
         c->acc_rows_per_chunk = RS * it;
         c->acc_n_chunks = (c->D + c->acc_rows_per_chunk - 1) / c->acc_rows_per_chunk;
         c->acc_ctas_per_pair = c->acc_n_chunks;
@@ -507,6 +510,18 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         c->acc_ctas_per_pair = c->acc_n_chunks * dft_col_tiles(L);
     }
     c->acc_nblk = c->P * c->acc_ctas_per_pair;
+
+    // kernels' shared-memory limits are raised here, for this geometry, outside any graph capture
+    {
+        cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e, c->fft_nt, c->rows_per_chunk)
+                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)
+                        : dft_prepare_f32(N);
+        if (e == cudaSuccess)
+            e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e, 256, c->acc_rows_per_chunk) : dft_prepare_f64(N);
+        if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
+        if (e == cudaSuccess && c->K <= 8192) e = rho_prepare(c->K);
+        if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
+    }
     const size_t MN = (size_t)M * N;
     if ((s = dalloc(c, &c->pkey, c->nblk)) || (s = dalloc(c, &c->pidx, c->nblk)) ||
         (s = dalloc(c, &c->pvmax, c->nblk)) || (s = dalloc(c, &c->psum, c->nblk)) ||
@@ -604,6 +619,7 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
     a.pkey = c->pkey; a.pidx = c->pidx; a.pvmax = c->pvmax; a.psum = c->psum; a.pchi = c->pchi;
     a.cdiag = c->cdiag;
     a.fft_e = c->fft_e;
+    a.fft_nt = c->fft_nt;
     a.pdl = c->pdl ? 1 : 0;
     return a;
 }

@@ -76,6 +76,42 @@ def test_ambiguity_fft_matches_oracle(api, orc, case, elems, monkeypatch):
     assert err <= CHI_TOL * N, err / N
 
 
+WIDE_CASES = [
+    # M, N, L, k_lo, k_hi, nu0: rows of >= 1024 bins, where 512-thread CTAs are built
+    (2, 200, 1024, -60, 80, -0.5),
+    (2, 256, 2048, -255, 255, -0.5),
+    (3, 700, 2048, -699, 699, 0.0017),  # several chunks per pair, ragged tail, offset grid
+    (1, 64, 4096, -10, 10, -0.5),
+    (2, 2500, 1024, -300, 300, -0.5),  # N > L: folded products, the h window spans 3 L
+]
+
+
+@pytest.mark.parametrize("elems", ["16", "32"])
+@pytest.mark.parametrize("case", WIDE_CASES)
+def test_ambiguity_fft_512_thread_ctas(api, orc, case, elems, monkeypatch):
+    """512-thread CTAs (eight or four rows per step sharing x, the h window
+    and the twiddles) against the oracle: the grid and the fused maxima."""
+    monkeypatch.setenv("SQNGD_FFT_E", elems)
+    monkeypatch.setenv("SQNGD_FFT_NT", "512")
+    M, N, L, k_lo, k_hi, nu0 = case
+    nu = nu0 + np.arange(L) / L
+    x, h = _pair(orc, 300 + N, M, N)
+    ctx = _ctx(api, M, N, 4, nu, k_lo, k_hi)
+    assert ctx.path == api.AF_PATH_FFT
+    chi = ctx.af_ambiguity(_dev(x), _dev(h)).cpu().numpy()
+    ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
+    assert np.max(np.abs(chi - ref)) <= CHI_TOL * N
+    terms, _, _ = ctx.af_loss_grad_xh(_dev(x), _dev(h))
+    ctx.af_sync()
+    t = terms.cpu().numpy()
+    r = orc.loss(x, h, nu, k_lo, k_hi)
+    for gi, key in ((2, "wapsl"), (3, "wcpsl")):
+        if r[key] > 0:
+            assert abs(20 * np.log10(t[gi] / r[key])) <= DB_TOL, key
+        else:
+            assert t[gi] == 0.0, key                  # an empty class (one waveform: no cross pairs)
+
+
 DFT_CASES = [
     # M, N, nu, k_lo, k_hi
     (2, 100, wl.window_grid(0.05, 64), -40, 40),
