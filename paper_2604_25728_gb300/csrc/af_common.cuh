@@ -28,6 +28,15 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
     return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+
+// 2^x by the hardware's approximate base-2 exponential (PTX ex2.approx, results
+// below the normal range flushed to zero): for the per-cell terms of the
+// p-norm sums, each at most 1 and summed in FP32.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return mk(a.x * s, a.y * s); }
 // multiply by +j
 template <typename C> __device__ __forceinline__ C cmulj(C a) { return mk(-a.y, a.x); }

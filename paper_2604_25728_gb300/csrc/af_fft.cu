@@ -35,15 +35,6 @@ __device__ __forceinline__ bool better(K a, long long ia, K b, long long ib) {
     return a > b || (a == b && ia < ib);
 }
 
-__device__ __forceinline__ void pnorm_add(float hp, float kf, float& pv, float& ps) {
-    if (kf > pv) {
-        ps = (pv > 0.f ? ps * exp2f(hp * __log2f(pv / kf)) : 0.f) + 1.f;
-        pv = kf;
-    } else if (pv > 0.f) {
-        ps += exp2f(hp * __log2f(kf / pv));
-    }
-}
-
 __device__ __forceinline__ void pnorm_merge(float hp, float& pv, float& ps, float ov, float os) {
     const float nv = fmaxf(pv, ov);
     const float sa = (pv > 0.f) ? ps * exp2f(hp * __log2f(pv / nv)) : 0.f;
@@ -172,7 +163,7 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     K best = (K)-1;
     int best_li = 0;                          // (d - d_begin) * L + bin
     C best_c = zero;                          // chi at that cell
-    float pv = 0.f, ps = 0.f;                 // p-norm partials (key domain)
+    float pv = 0.f, ps = 0.f, ipv = 0.f;      // p-norm partials (key domain): max key, sum of (key/pv)^hp, 1/pv
 
     for (int d0 = d_begin; d0 < d_end; d0 += RS) {
         const int d = d0 + slot;
@@ -225,9 +216,46 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                             key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
                         }
                         if (key > best) { best = key; best_li = lbase + off; best_c = c; }
-                        if constexpr (MODE == MODE_REDUCE_PNORM) {
-                            if (key >= (K)0) pnorm_add(a.half_p, (float)key, pv, ps);
+                    }
+                }
+                if constexpr (MODE == MODE_REDUCE_PNORM) {
+                    // the p-norm partial of this thread's cells of the row: their
+                    // largest key first (one rescale of the running sum at most),
+                    // then sum (key/pv)^hp with no branch per cell
+                    float kmax = -1.f;
+#pragma unroll
+                    for (int r = 0; r < RL; ++r)
+#pragma unroll
+                        for (int s = 0; s < NBL; ++s) {
+                            const C c = v[s * RL + r];
+                            float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
+                            if constexpr (decltype(weighted)::value) {
+                                const float w = __ldg(wrow + TPR * s + r * NSL);
+                                key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : -1.f;
+                            }
+                            kmax = fmaxf(kmax, key);
                         }
+                    if (kmax > pv) {
+                        ps = (pv > 0.f) ? ps * exp2f(a.half_p * __log2f(pv / kmax)) : 0.f;
+                        pv = kmax;
+                        ipv = 1.f / kmax;
+                    }
+                    if (pv > 0.f) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int r = 0; r < RL; ++r)
+#pragma unroll
+                            for (int s = 0; s < NBL; ++s) {
+                                const C c = v[s * RL + r];
+                                float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
+                                if constexpr (decltype(weighted)::value) {
+                                    const float w = __ldg(wrow + TPR * s + r * NSL);
+                                    key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : 0.f;
+                                }
+                                // key = 0 gives log2 = -inf and a zero term
+                                acc += ex2_approx(a.half_p * __log2f(key * ipv));
+                            }
+                        ps += acc;
                     }
                 }
             };

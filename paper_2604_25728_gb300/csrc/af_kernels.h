@@ -47,11 +47,17 @@ struct FwdArgs {
     int pdl;               // launch with programmatic stream serialisation
 };
 
-// Dense adjoint of the p-norm sidelobe loss on the FFT grid (same launch
-// geometry as the forward pass).
+// Dense adjoint of the p-norm sidelobe loss on the FFT grid.  The grid spans
+// only the winning class: `grid` CTAs, chunk b mod cpp_cls[c] of pair
+// b / cpp_cls[c] of class c.
 struct AdjArgs {
     int M, N, L, D, k_lo;
-    int n_chunks, rows_per_chunk;
+    int grid;              // CTAs of the launch (the same for either winning class)
+    int cpp_cls[2];        // delay chunks per pair when the auto (0) / cross (1) class wins
+    int rows_cls[2];       // delays per chunk (a multiple of the row slots)
+    int rpc_max;           // the larger of the two (sizes the h window)
+    int nt;                // threads per CTA (256, or 512 for rows of >= 1024 bins)
+    int* cls_buf;          // the winning class, written by CTA 0 for the summing kernel
     const float2* x;       // [M][N] waveforms of this evaluation
     const float2* h;       // [M][N] filters
     const float2* pre;     // [N] e^{j 2 pi nu_0 n}
@@ -69,9 +75,14 @@ struct AdjArgs {
     int fft_e;
     int pdl;
 };
+struct AdjGeom {
+    int grid, cpp[2], rows[2], rpc_max;
+};
 cudaError_t launch_adj(const AdjArgs& a, cudaStream_t s);
-cudaError_t adj_prepare(int L, int N, int E);
-int adj_smem_bytes(int L, int N, int E);
+cudaError_t adj_prepare(int L, int N, int E, int NT, int rpc);
+int adj_smem_bytes(int L, int N, int E, int NT, int rpc);
+int adj_threads(int L, int E);
+void adj_geometry(int M, int D, int L, int E, int NT, int slots, AdjGeom* g);
 
 // FFT path with E values per thread: dynamic shared memory bytes (-1 if L
 // unsupported), row slots per 256-thread CTA, and the default E for L.

@@ -144,7 +144,12 @@ struct af_ctx {
     float* pvmax = nullptr;
     float* psum = nullptr;
     float2* pchi = nullptr;    // [nblk] chi at each forward CTA's best cell
-    float2* adj_part = nullptr;    // [nblk][2][N] dense-adjoint partial rows (p-norm loss)
+    float2* adj_part = nullptr;    // [adj grid][2][N] dense-adjoint partial rows (p-norm loss)
+    int* adj_cls = nullptr;        // the winning class of the last dense adjoint
+    int adj_nt = 256;              // threads per dense-adjoint CTA
+    int adj_e = 0;                 // values per thread of the dense adjoint's transforms
+    float2* tw_adj = nullptr;      // its twiddles (when they differ from the forward's)
+    AdjGeom adj_geom{};            // dense-adjoint grid (the winning class only)
     float2* dense = nullptr;       // [2][M][N] summed dense sidelobe gradient
     double* pkey64 = nullptr;
     long long* pidx64 = nullptr;
@@ -235,7 +240,7 @@ static void free_all(af_ctx* c) {
     void* ptrs[] = {c->pre, c->tw, c->wL, c->E, c->pre64, c->tw64, c->E64, c->wmap, c->rho, c->level,
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
                     c->xs, c->xs2, c->m_rho, c->v_rho, c->rho_acc, c->du, c->gy, c->zb, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
-                    c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->dense,
+                    c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->adj_cls, c->dense, c->tw_adj,
                     c->bimg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -341,9 +346,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     for (int j = 0; uniform && j < L; ++j)
         if (fabs(c->nu[j] - (c->nu0 + (double)j / L)) > 1e-12) uniform = false;
     c->fft_e = uniform ? fft_default_elems(L, false) : 0;
-    // the dense adjoint of the p-norm loss shares the forward's twiddle
-    // tables and is built for 8 and 16 values per thread
-    if (cfg->pnorm > 0.0 && c->fft_e == 32) c->fft_e = 16;
+    // the dense adjoint of the p-norm loss is built for 8 and 16 values per
+    // thread (it holds two transforms' operands and a gradient row in registers)
+    c->adj_e = (c->fft_e == 32) ? 16 : c->fft_e;
     c->fft_nt = uniform ? fft_default_threads(L, c->fft_e, false) : 256;
     if (uniform && c->fft_nt != 256) {
         const int wide = fft_smem_bytes(L, N, false, c->fft_e, c->fft_nt);
@@ -382,8 +387,19 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     }
     c->grid_fft = uniform;
     if (cfg->pnorm > 0.0) {
-        // the dense adjoint of the p-norm loss runs on the FFT grid
-        const int adj = (c->path == AF_PATH_FFT) ? adj_smem_bytes(L, N, c->fft_e) : -1;
+        // the dense adjoint of the p-norm loss runs on the FFT grid; its grid
+        // spans the winning class only, its CTA as wide as shared memory allows
+        int sms_a = 0;
+        if (cudaDeviceGetAttribute(&sms_a, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms_a < 1)
+            sms_a = 1;
+        int adj = -1;
+        for (int nt : {adj_threads(L, c->adj_e), 256}) {
+            if (c->path != AF_PATH_FFT) break;
+            c->adj_nt = nt;
+            adj_geometry(M, c->D, L, c->adj_e, nt, sms_a, &c->adj_geom);
+            adj = adj_smem_bytes(L, N, c->adj_e, nt, c->adj_geom.rpc_max);
+            if (adj > 0 && adj <= 227 * 1024) break;
+        }
         if (adj <= 0 || adj > 227 * 1024) {
             c->err = "pnorm > 0 needs the FFT path (uniform grid) with the adjoint fitting in shared memory";
             return fail(AF_ERR_UNIMPLEMENTED);
@@ -441,6 +457,13 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         std::vector<float2> tw(t32.size());
         for (size_t i = 0; i < t32.size(); ++i) tw[i] = make_float2((float)t32[i].x, (float)t32[i].y);
         if ((s = upload(c, &c->tw, tw)) || (s = upload(c, &c->tw64, t64))) return fail(s);
+        if (cfg->pnorm > 0.0 && c->adj_e != c->fft_e) {
+            std::vector<double2> ta;
+            twiddles(c->adj_e, ta);
+            std::vector<float2> twa(ta.size());
+            for (size_t i = 0; i < ta.size(); ++i) twa[i] = make_float2((float)ta[i].x, (float)ta[i].y);
+            if ((s = upload(c, &c->tw_adj, twa))) return fail(s);
+        }
     }
     {
         // phasor table of the arbitrary-grid path (also used for acceptance when
@@ -518,7 +541,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
                         : dft_prepare_f32(N);
         if (e == cudaSuccess)
             e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e, 256, c->acc_rows_per_chunk) : dft_prepare_f64(N);
-        if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->fft_e);
+        if (e == cudaSuccess && cfg->pnorm > 0.0) e = adj_prepare(L, N, c->adj_e, c->adj_nt, c->adj_geom.rpc_max);
         if (e == cudaSuccess && c->K <= 8192) e = rho_prepare(c->K);
         if (e != cudaSuccess) { c->err = std::string("kernel attribute: ") + cudaGetErrorString(e); return fail(AF_ERR_CUDA); }
     }
@@ -537,7 +560,8 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         (s = dalloc(c, &c->errflag, 1)) || (s = dalloc(c, &c->ctr, 4)) || (s = dalloc(c, &c->best2, 8)))
         return fail(s);
     if (cfg->pnorm > 0.0 &&
-        ((s = dalloc(c, &c->adj_part, (size_t)c->nblk * 2 * N)) || (s = dalloc(c, &c->dense, 2 * MN))))
+        ((s = dalloc(c, &c->adj_part, (size_t)c->adj_geom.grid * 2 * N)) || (s = dalloc(c, &c->dense, 2 * MN)) ||
+         (s = dalloc(c, &c->adj_cls, 1))))
         return fail(s);
     if (c->rho_acc && cudaMemset(c->rho_acc, 0, sizeof(long long) * c->K) != cudaSuccess) {
         c->err = "cudaMemset failed";
@@ -654,14 +678,19 @@ static cudaError_t launch_eval_forward(af_ctx* c, const float2* x, const float2*
     if (e != cudaSuccess || !(c->cfg.pnorm > 0.0) || !adjoint) return e;
     AdjArgs d{};
     d.M = c->cfg.M; d.N = c->cfg.N; d.L = c->cfg.L; d.D = c->D; d.k_lo = c->cfg.k_lo;
-    d.n_chunks = c->n_chunks; d.rows_per_chunk = c->rows_per_chunk;
-    d.x = x; d.h = h; d.pre = c->pre; d.tw = c->tw;
+    d.grid = c->adj_geom.grid;
+    d.cpp_cls[0] = c->adj_geom.cpp[0]; d.cpp_cls[1] = c->adj_geom.cpp[1];
+    d.rows_cls[0] = c->adj_geom.rows[0]; d.rows_cls[1] = c->adj_geom.rows[1];
+    d.rpc_max = c->adj_geom.rpc_max;
+    d.nt = c->adj_nt;
+    d.cls_buf = c->adj_cls;
+    d.x = x; d.h = h; d.pre = c->pre; d.tw = c->tw_adj ? c->tw_adj : c->tw;
     d.wmap = c->wmap; d.weight_mode = c->wmap ? WM_MAP : WM_UNIFORM; d.w0 = c->w0;
     d.eps = c->cfg.eps; d.half_p = (float)(c->cfg.pnorm * 0.5);
     d.nblk_fwd = c->nblk; d.ctas_per_pair_fwd = c->ctas_per_pair;
     d.pvmax = c->pvmax; d.psum = c->psum;
     d.part = c->adj_part; d.dense = c->dense;
-    d.fft_e = c->fft_e; d.pdl = c->pdl ? 1 : 0;
+    d.fft_e = c->adj_e; d.pdl = c->pdl ? 1 : 0;
     return launch_adj(d, s);
 }
 

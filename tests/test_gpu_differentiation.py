@@ -103,13 +103,14 @@ def test_autograd_gradient_matches_finite_differences_at_full_size(api, orc, pno
     ctx.close()
 
 
-@pytest.mark.parametrize("pn", [8.0, 16.0])
+@pytest.mark.parametrize("pn", [7.0, 8.0, 16.0])
 @pytest.mark.parametrize("L", [1024, 2048])
 def test_dense_adjoint_at_large_transforms_default_radix(api, orc, L, pn):
     """The p-norm loss and its dense adjoint, element by element, at the
     transform lengths of the differentiation workload's launch shapes with
-    the library's own choice of radix (no override), every delay."""
-    M, N = 2, 600
+    the library's own choice of radix and CTA width (no override), every
+    delay; p = 7 takes the general power, even p the multiplication-only one."""
+    M, N = 3, 600
     nu = wl.full_grid(L)
     x = wl.unit_phasors(600 + L, M, N).astype(np.complex64)
     h = orc.project(x.astype(np.complex128) + 0.3 * wl.complex_normal(600 + L, M, N)).astype(np.complex64)

@@ -492,7 +492,7 @@ PNORM_CASES = [
 
 
 @pytest.mark.parametrize("elems", ["8", "16"])
-@pytest.mark.parametrize("pn", [8.0, 16.0])
+@pytest.mark.parametrize("pn", [5.0, 8.0, 16.0])
 @pytest.mark.parametrize("case", PNORM_CASES)
 def test_pnorm_loss_and_dense_gradient(api, orc, case, pn, elems, monkeypatch):
     """Smooth p-norm sidelobe loss: every cell of the winning class carries
