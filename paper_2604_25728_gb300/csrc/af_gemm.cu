@@ -1,12 +1,16 @@
 // af_gemm.cu -- forward pass on a narrow Doppler window as a tensor-core
 // contraction (sm_103a, tcgen05 + tensor memory).
 //
-// chi[(pair, d), j] = sum_n P[(pair, d), n] E[n, j]   (Eq. 6 restated per row)
-// with P = x_m(n) conj(h_l(n+k)) the lag products and E[n, j] = e^{j 2 pi nu_j n}.
-// Complex arithmetic is embedded in a real GEMM: the K index interleaves
-// (Re P(n), Im P(n)) and the output columns interleave (Re chi_j, Im chi_j),
-// so B[(n,0),(j,0)] = cos, B[(n,1),(j,0)] = -sin, B[(n,0),(j,1)] = sin,
-// B[(n,1),(j,1)] = cos of 2 pi nu_j n.
+// chi[(pair, d), j] = sum_n conj(h_l(n+k)) [x_m(n) e^{j 2 pi nu_j n}]
+// (Eq. 6 restated per row): a product A B with A[(pair, d), n] =
+// conj(h_l(n + k)) -- a Hankel matrix of the filter, the same for every
+// transmit waveform -- and B_m[n, j] = x_m(n) E[n, j], E[n, j] = e^{j 2 pi nu_j n},
+// one image per transmit waveform, built for each evaluation by
+// gemm_bimg_kernel from x and the FP64-built phasor table.  Complex arithmetic
+// is embedded in a real GEMM: the K index interleaves (Re A(n), Im A(n)) and
+// the output columns interleave (Re chi_j, Im chi_j), so with b = B_m[n, j]
+// B[(n,0),(j,0)] = Re b, B[(n,1),(j,0)] = -Im b, B[(n,0),(j,1)] = Im b,
+// B[(n,1),(j,1)] = Re b.
 //
 // Precision: both operands are split into BF16 pairs v = hi + lo and the
 // product is taken as Ah Bh + Ah Bl + Al Bh (the lo*lo term is below FP32
@@ -14,13 +18,14 @@
 //
 // One CTA owns 128 consecutive delays of one pair (the MMA M) and LB bins
 // (N = 2 LB columns).  Roles:
-//   warps 0-3  form the lag products of their row (thread = row = TMEM lane)
-//              for a chunk of 32 samples, split them and store them into a
-//              tensor-memory A stage (tcgen05.st); afterwards they read the
-//              accumulator back (tcgen05.ld) and run the sidelobe reduction.
+//   warps 0-3  copy their row's split filter samples (thread = row = TMEM
+//              lane; the CTA splits its window of conj(h_l) into BF16 hi/lo
+//              once) for a chunk of 32 samples into a tensor-memory A stage
+//              (tcgen05.st); afterwards they read the accumulator back
+//              (tcgen05.ld) and run the sidelobe reduction.
 //   warp 4     allocates tensor memory; lane 0 issues the MMAs.
-//   warp 5     lane 0 streams the precomputed B images (hi | lo, already in
-//              the canonical no-swizzle K-major layout) with cp.async.bulk.
+//   warp 5     lane 0 streams the pair's B_m image (hi | lo, in the canonical
+//              no-swizzle K-major layout) with cp.async.bulk.
 // Stages are double-buffered with mbarriers; every wait is bounded and a
 // timeout sets bit 1 of the error flag and ends the kernel cleanly.
 #include <cuda_bf16.h>
@@ -132,8 +137,8 @@ fwd_gemm_kernel(const GemmArgs g) {
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* bst = smem_raw;                                        // [kSB][STAGE_BYTES]
-    const int XH = 2 * kSPC * g.n_kc + kTM;                               // per tile: xs, then hs
-    float2* xh_base = reinterpret_cast<float2*>(smem_raw + kSB * STAGE_BYTES);
+    const int XH = kSPC * g.n_kc + kTM;                                   // per tile: split conj(h) window
+    uint2* xh_base = reinterpret_cast<uint2*>(smem_raw + kSB * STAGE_BYTES);
 
     __shared__ __align__(8) uint64_t bfull[kSB], bempty[kSB], afull[kSA], aempty[kSA], accfull, never;
     __shared__ uint32_t s_tmem;
@@ -188,8 +193,10 @@ fwd_gemm_kernel(const GemmArgs g) {
     const uint32_t tbase = s_tmem;
     volatile int* abort_flag = &s_abort;
 
+    // the T pairs of a CTA share their transmit waveform (T divides M), so one B_m image
+    const int m_cta = (pg * T) / a.M;
     const unsigned char* img = reinterpret_cast<const unsigned char*>(g.bimg) +
-                               ((size_t)ct * g.n_kc + c0) * (size_t)STAGE_BYTES;
+                               (((size_t)m_cta * g.n_ct + ct) * g.n_kc + c0) * (size_t)STAGE_BYTES;
 
     if (warp == WLOAD) {
         // ---------------------------------------------------- B loader --
@@ -199,15 +206,14 @@ fwd_gemm_kernel(const GemmArgs g) {
             tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
         };
         int issued = 0;
+        // the B_m images are written by the kernel just ahead in the stream
+        pdl_wait();
+        pdl_trigger();
         if (lane == 0) {
-            // the tables are constant: the first stages load before the
-            // previous kernel in the stream has finished
             const int pro = min(kSB, nch);
             for (int i = 0; i < pro; ++i) issue(i, i);
             issued = pro;
         }
-        pdl_wait();
-        pdl_trigger();
         if (lane == 0) {
             for (int i = kSB; i < nch; ++i) {
                 const int s = i % kSB;
@@ -272,27 +278,28 @@ fwd_gemm_kernel(const GemmArgs g) {
         const int pair = pg * T + t;
         const int m = pair / a.M, l = pair - m * a.M;
         const int ob = (pair * a.n_chunks + tile) * g.n_ct + ct;   // partial record (pair-major)
-        float2* xs = xh_base + t * XH;                   // [kSPC * n_kc]
-        float2* hs = xs + kSPC * g.n_kc;                 // [kSPC * n_kc + kTM]
+        uint2* hs = xh_base + t * XH;                    // [kSPC * n_kc + kTM] split conj(h_l) window
         const float2* xm = a.x + (size_t)m * N;
         const float2* hl = a.h + (size_t)l * N;
-        const int nx = kSPC * nch, nh = kSPC * nch + kTM;
-        // all loads of a batch are in flight before the first store
+        const int nh = kSPC * nch + kTM;
+        // the window conj(h_l(p)), p = SPC c0 + k_first + i, split once into
+        // BF16 (re, im) hi and lo pairs: all loads of a batch are in flight
+        // before the first store
         constexpr int FB = 8;
         for (int i0 = r; i0 < nh; i0 += kTM * FB) {
-            float2 hv[FB], xv[FB];
+            float2 hv[FB];
 #pragma unroll
             for (int q = 0; q < FB; ++q) {
                 const int i = i0 + q * kTM;
-                const int p = kSPC * c0 + k_first + i, n = kSPC * c0 + i;
+                const int p = kSPC * c0 + k_first + i;
                 hv[q] = (i < nh && p >= 0 && p < N) ? hl[p] : make_float2(0.f, 0.f);
-                xv[q] = (i < nx && n < N) ? xm[n] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int q = 0; q < FB; ++q) {
                 const int i = i0 + q * kTM;
-                if (i < nh) hs[i] = hv[q];
-                if (i < nx) xs[i] = xv[q];
+                const float re = hv[q].x, im = -hv[q].y;
+                const uint32_t ph = pack_bf16(re, im);
+                if (i < nh) hs[i] = make_uint2(ph, pack_bf16(re - bf16_lo_f(ph), im - bf16_hi_f(ph)));
             }
         }
         // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) (SNRL, Eq. 38) while the first
@@ -337,17 +344,14 @@ fwd_gemm_kernel(const GemmArgs g) {
                 if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
                 tc::fence_after_sync();
             }
+            // row r, sample n = SPC (c0 + i) + u: conj(h_l(n + k)) = hs[SPC i + r + u]
             uint32_t hi[kSPC], lo[kSPC];
-            const float2* xc = xs + i * kSPC;
-            const float2* hc = hs + i * kSPC + r;
+            const uint2* hc = hs + i * kSPC + r;
 #pragma unroll
             for (int u = 0; u < kSPC; ++u) {
-                const float2 xv = xc[u], hv = hc[u];
-                const float re = fmaf(xv.x, hv.x, xv.y * hv.y);
-                const float im = fmaf(xv.y, hv.x, -(xv.x * hv.y));
-                const uint32_t ph = pack_bf16(re, im);
-                hi[u] = ph;
-                lo[u] = pack_bf16(re - bf16_lo_f(ph), im - bf16_hi_f(ph));
+                const uint2 hv = hc[u];
+                hi[u] = hv.x;
+                lo[u] = hv.y;
             }
             const uint32_t acol = trow + T * NC + (s * T + t) * kKC;
             tmem_st<kSPC>(acol, hi);
@@ -454,6 +458,76 @@ fwd_gemm_kernel(const GemmArgs g) {
     }
 }
 
+// B_m images of one evaluation (see the top of this file): thread (m, ct, c,
+// jj, g) writes, for bin j = ct LB + jj and samples n = c SPC + 4 g .. + 3,
+// the two 16-byte core-matrix rows (u = 0, 1) of the hi and of the lo image.
+// Row u = 0 holds (Re b, -Im b) per sample, row u = 1 (Im b, Re b), with
+// b = x_m(n) E[n, j] in FP32 (E built in FP64 on the host); bins beyond L and
+// samples beyond N are zero.
+__global__ void gemm_bimg_kernel(const float2* __restrict__ x, const float2* __restrict__ E, int M, int N, int L,
+                                 int LB, int n_ct, int n_kc, int spc, uint16_t* __restrict__ img) {
+    pdl_wait();
+    pdl_trigger();
+    const int G = spc / 4;
+    const long long total = (long long)M * n_ct * n_kc * LB * G;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    const int jj = (int)(id % LB);
+    long long rest = id / LB;
+    const int g = (int)(rest % G); rest /= G;
+    const int c = (int)(rest % n_kc); rest /= n_kc;
+    const int ct = (int)(rest % n_ct);
+    const int m = (int)(rest / n_ct);
+    const int j = ct * LB + jj;
+    const int NC = 2 * LB, KC = 2 * spc;
+    float re[4], im[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int n = c * spc + 4 * g + q;
+        float2 b = make_float2(0.f, 0.f);
+        if (n < N && j < L) b = cmul(x[(size_t)m * N + n], E[(size_t)n * L + j]);
+        re[q] = b.x;
+        im[q] = b.y;
+    }
+    uint16_t* hi_img = img + ((((size_t)m * n_ct + ct) * n_kc + c) * 2) * (size_t)NC * KC;
+    uint16_t* lo_img = hi_img + (size_t)NC * KC;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        uint32_t h4[4], l4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float v0 = (u == 0) ? re[q] : im[q];    // K index 2 s    (Re A)
+            const float v1 = (u == 0) ? -im[q] : re[q];   // K index 2 s + 1 (Im A)
+            const uint32_t ph = pack_bf16(v0, v1);
+            h4[q] = ph;
+            l4[q] = pack_bf16(v0 - bf16_lo_f(ph), v1 - bf16_hi_f(ph));
+        }
+        const int ci = 2 * jj + u;
+        // core matrix (ci / 8, g) of 8 x 8 BF16, row ci % 8: 16 contiguous bytes
+        const size_t off = (size_t)(ci / 8) * (KC / 8) * 64 + (size_t)g * 64 + (ci % 8) * 8;
+        *reinterpret_cast<uint4*>(hi_img + off) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
+        *reinterpret_cast<uint4*>(lo_img + off) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+    }
+}
+
+cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int spc, void* img, int pdl,
+                             cudaStream_t s) {
+    const int LB = gemm_bins_per_tile(L);
+    const int n_ct = (L + LB - 1) / LB, n_kc = (N + spc - 1) / spc;
+    if (spc % 4 != 0) return cudaErrorInvalidValue;
+    const long long total = (long long)M * n_ct * n_kc * LB * (spc / 4);
+    const int threads = 256;
+    const long long blocks = (total + threads - 1) / threads;
+    return launch_ex(gemm_bimg_kernel, dim3((unsigned)blocks), dim3(threads), 0, s, pdl != 0, x, E, M, N, L, LB,
+                     n_ct, n_kc, spc, reinterpret_cast<uint16_t*>(img));
+}
+
+size_t gemm_bimg_bytes(int M, int N, int L, int spc) {
+    const int LB = gemm_bins_per_tile(L);
+    const size_t n_ct = (L + LB - 1) / LB, n_kc = (N + spc - 1) / spc;
+    return (size_t)M * n_ct * n_kc * 2 * (size_t)(2 * LB) * (2 * spc) * sizeof(uint16_t);
+}
+
 int gemm_bins_per_tile(int L) {
     int lb = 16;
     while (lb < L && lb < 128) lb <<= 1;
@@ -468,7 +542,7 @@ int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles) {
     const int tcols = gemm_tmem_cols(NC, spc, sa, tiles);
     if (tcols == 0 || spc <= 0 || tiles < 1) return 0;
     const int n_kc = (N + spc - 1) / spc;
-    const int need = sb * NC * spc * 8 + tiles * (int)sizeof(float2) * (2 * spc * n_kc + kTM);
+    const int need = sb * NC * spc * 8 + tiles * (int)sizeof(uint2) * (spc * n_kc + kTM);
     const int floor_bytes = 228 * 1024 / (512 / tcols + 1) + 1024;
     const int b = need > floor_bytes ? need : floor_bytes;
     return b <= 227 * 1024 ? b : 0;

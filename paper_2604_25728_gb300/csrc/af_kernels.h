@@ -115,7 +115,7 @@ cudaError_t launch_fwd_dft_f64(const FwdArgs<double2, double>& a, cudaStream_t s
 constexpr int kGemmRows = 128;      // delays per tile (MMA M)
 struct GemmArgs {
     FwdArgs<float2, float> f;   // x, h, wmap, mode, pkey/pidx/pchi, cdiag, chi_out, ctr_inc, pdl
-    const void* bimg;           // [n_ct][n_kc][hi | lo][2 LB x 2 spc] BF16 images of E
+    const void* bimg;           // [M][n_ct][n_kc][hi | lo][2 LB x 2 spc] BF16 images of B_m = x_m E
     int* err;                   // bit 1 set when a pipeline wait timed out
     int n_ct;                   // column tiles = ceil(L / LB)
     int n_kc;                   // sample chunks = ceil(N / spc)
@@ -130,6 +130,10 @@ int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles);
 bool gemm_shape_supported(int L, int N, int spc, int sb, int sa, int tiles);
 cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles);
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
+// B_m = x_m(n) e^{j 2 pi nu_j n} images of one evaluation (E: [N][L] FP32 phasors)
+cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int spc, void* img, int pdl,
+                             cudaStream_t s);
+size_t gemm_bimg_bytes(int M, int N, int L, int spc);
 
 // Record the message of a failed call that has no context (read back by
 // af_last_error(NULL) on the same thread).

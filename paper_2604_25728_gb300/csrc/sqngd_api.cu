@@ -26,60 +26,6 @@ inline void phasor(double t, double* re, double* im) {
     *im = sin(kTwoPi * f);
 }
 
-// BF16 round-to-nearest-even of a finite float, and back.
-inline uint16_t bf16_rne(float f) {
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-inline float bf16_float(uint16_t b) {
-    const uint32_t u = (uint32_t)b << 16;
-    float f;
-    memcpy(&f, &u, 4);
-    return f;
-}
-
-// Images of the real-embedded DFT matrix for the tensor-core path, one per
-// (column tile, chunk of SPC samples), each [hi | lo] of 2 LB rows x 2 SPC K
-// in the canonical K-major no-swizzle layout: 8x8 BF16 core matrices, 128 B
-// apart along K, 2 SPC / 8 core matrices apart between row groups.  Row
-// 2j + u is output bin j (u = 0 real, 1 imaginary part), K index 2s + t is
-// sample s of the chunk (t = 0 real, 1 imaginary part of the lag product):
-//   (t,u) = (0,0): cos, (1,0): -sin, (0,1): sin, (1,1): cos  of 2 pi nu_j n.
-// Each value v (built in FP64) is stored as hi = bf16(v), lo = bf16(v - hi).
-void gemm_build_image(const std::vector<double>& nu, int N, int SPC, std::vector<uint16_t>& img) {
-    const int L = (int)nu.size();
-    const int LB = af::gemm_bins_per_tile(L), NC = 2 * LB, KC = 2 * SPC;
-    const int n_ct = (L + LB - 1) / LB, n_kc = (N + SPC - 1) / SPC;
-    const size_t part = (size_t)NC * KC;
-    img.assign((size_t)n_ct * n_kc * 2 * part, 0);
-    for (int ct = 0; ct < n_ct; ++ct)
-        for (int c = 0; c < n_kc; ++c) {
-            uint16_t* hi = img.data() + ((size_t)ct * n_kc + c) * 2 * part;
-            uint16_t* lo = hi + part;
-            for (int sm = 0; sm < SPC; ++sm) {
-                const int n = c * SPC + sm;
-                if (n >= N) break;
-                for (int j = 0; j < LB; ++j) {
-                    const int jj = ct * LB + j;
-                    if (jj >= L) break;
-                    double cs, sn;
-                    phasor(nu[jj] * n, &cs, &sn);
-                    const double val[2][2] = {{cs, sn}, {-sn, cs}};   // [t][u]
-                    for (int t = 0; t < 2; ++t)
-                        for (int u = 0; u < 2; ++u) {
-                            const int ci = 2 * j + u, kk = 2 * sm + t;
-                            const size_t off = (size_t)(ci / 8) * (KC / 8) * 64 + (kk / 8) * 64 + (ci % 8) * 8 + kk % 8;
-                            const uint16_t h16 = bf16_rne((float)val[t][u]);
-                            hi[off] = h16;
-                            lo[off] = bf16_rne((float)(val[t][u] - (double)bf16_float(h16)));
-                        }
-                }
-            }
-        }
-}
-
 struct FftPassInfo { int R, NS; };
 
 // Host mirror of the device FFT plan (radix-E passes, then the remainder).
@@ -117,7 +63,7 @@ struct af_ctx {
     float2* tw = nullptr;      // FFT twiddles
     float2* wL = nullptr;      // [L] e^{j 2 pi i / L}
     float2* E = nullptr;       // [N][L] e^{j 2 pi nu_j n} (DFT path)
-    uint16_t* bimg = nullptr;  // BF16 hi/lo images of E (tensor-core path)
+    uint16_t* bimg = nullptr;  // BF16 hi/lo images of B_m = x_m E, rebuilt per evaluation (tensor-core path)
     int gemm_n_ct = 0, gemm_n_kc = 0;
     int gemm_spc = 32, gemm_sb = 2, gemm_sa = 2;   // samples per stage, B stages, A stages
     int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
@@ -480,9 +426,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         if ((s = upload(c, &c->E, E)) || (s = upload(c, &c->E64, E64))) return fail(s);
     }
     if (c->path == AF_PATH_SPLIT_BF16) {
-        std::vector<uint16_t> img;
-        gemm_build_image(c->nu, N, c->gemm_spc, img);
-        if ((s = upload(c, &c->bimg, img))) return fail(s);
+        if ((s = dalloc(c, &c->bimg, gemm_bimg_bytes(M, N, L, c->gemm_spc) / sizeof(uint16_t)))) return fail(s);
         const int LB = gemm_bins_per_tile(L);
         c->gemm_n_ct = (L + LB - 1) / LB;
         c->gemm_n_kc = (N + c->gemm_spc - 1) / c->gemm_spc;
@@ -650,6 +594,9 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
 
 static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaStream_t s) {
     if (c->path == AF_PATH_SPLIT_BF16) {
+        // this evaluation's B_m images, then the contraction
+        cudaError_t e = launch_gemm_bimg(a.x, c->E, c->cfg.M, c->cfg.N, c->cfg.L, c->gemm_spc, c->bimg, a.pdl, s);
+        if (e != cudaSuccess) return e;
         GemmArgs g{};
         g.f = a;
         g.bimg = c->bimg;
