@@ -510,9 +510,8 @@ __global__ void gemm_bimg_kernel(const float2* __restrict__ x, const float2* __r
     }
 }
 
-cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int spc, void* img, int pdl,
-                             cudaStream_t s) {
-    const int LB = gemm_bins_per_tile(L);
+cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int LB, int spc, void* img,
+                             int pdl, cudaStream_t s) {
     const int n_ct = (L + LB - 1) / LB, n_kc = (N + spc - 1) / spc;
     if (spc % 4 != 0) return cudaErrorInvalidValue;
     const long long total = (long long)M * n_ct * n_kc * LB * (spc / 4);
@@ -522,12 +521,12 @@ cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int
                      n_ct, n_kc, spc, reinterpret_cast<uint16_t*>(img));
 }
 
-size_t gemm_bimg_bytes(int M, int N, int L, int spc) {
-    const int LB = gemm_bins_per_tile(L);
+size_t gemm_bimg_bytes(int M, int N, int L, int LB, int spc) {
     const size_t n_ct = (L + LB - 1) / LB, n_kc = (N + spc - 1) / spc;
     return (size_t)M * n_ct * n_kc * 2 * (size_t)(2 * LB) * (2 * spc) * sizeof(uint16_t);
 }
 
+// The widest column tile: the smallest power of two >= L, from 16 to 128 bins.
 int gemm_bins_per_tile(int L) {
     int lb = 16;
     while (lb < L && lb < 128) lb <<= 1;
@@ -537,8 +536,9 @@ int gemm_bins_per_tile(int L) {
 // Dynamic shared memory of a CTA (0 if the shape does not fit).  It is padded
 // so that the CTAs that fit on an SM never ask for more tensor memory than the
 // SM's 512 columns, so no allocation has to wait.
-int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles) {
-    const int NC = 2 * gemm_bins_per_tile(L);
+int gemm_smem_bytes(int LB, int N, int spc, int sb, int sa, int tiles) {
+    const int NC = 2 * LB;
+    if (!(LB == 16 || LB == 32 || LB == 64 || LB == 128)) return 0;
     const int tcols = gemm_tmem_cols(NC, spc, sa, tiles);
     if (tcols == 0 || spc <= 0 || tiles < 1) return 0;
     const int n_kc = (N + spc - 1) / spc;
@@ -592,18 +592,18 @@ static cudaError_t launch_nc(const GemmArgs& g, int smem, cudaStream_t s, bool p
     return g.tiles == 2 ? launch_nct<NC, 2>(g, smem, s, prepare_only) : launch_nct<NC, 1>(g, smem, s, prepare_only);
 }
 
-bool gemm_shape_supported(int L, int N, int spc, int sb, int sa, int tiles) {
+bool gemm_shape_supported(int LB, int N, int spc, int sb, int sa, int tiles) {
     bool listed = false;
 #define AF_GEMM_LISTED(P, B, A) listed = listed || (spc == P && sb == B && sa == A);
     AF_GEMM_SHAPES(AF_GEMM_LISTED)
 #undef AF_GEMM_LISTED
-    return listed && (tiles == 1 || tiles == 2) && gemm_smem_bytes(L, N, spc, sb, sa, tiles) > 0;
+    return listed && (tiles == 1 || tiles == 2) && gemm_smem_bytes(LB, N, spc, sb, sa, tiles) > 0;
 }
 
 static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only) {
-    if (!gemm_shape_supported(g.f.L, g.f.N, g.spc, g.sb, g.sa, g.tiles)) return cudaErrorInvalidValue;
-    const int smem = gemm_smem_bytes(g.f.L, g.f.N, g.spc, g.sb, g.sa, g.tiles);
-    switch (2 * gemm_bins_per_tile(g.f.L)) {
+    if (!gemm_shape_supported(g.lb, g.f.N, g.spc, g.sb, g.sa, g.tiles)) return cudaErrorInvalidValue;
+    const int smem = gemm_smem_bytes(g.lb, g.f.N, g.spc, g.sb, g.sa, g.tiles);
+    switch (2 * g.lb) {
         case 32: return launch_nc<32>(g, smem, s, prepare_only);
         case 64: return launch_nc<64>(g, smem, s, prepare_only);
         case 128: return launch_nc<128>(g, smem, s, prepare_only);
@@ -612,9 +612,9 @@ static cudaError_t dispatch(const GemmArgs& g, cudaStream_t s, bool prepare_only
     }
 }
 
-cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles) {
+cudaError_t gemm_prepare(int LB, int N, int spc, int sb, int sa, int tiles) {
     GemmArgs g{};
-    g.f.L = L;
+    g.lb = LB;
     g.f.N = N;
     g.spc = spc;
     g.sb = sb;
@@ -624,7 +624,8 @@ cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles) {
 }
 
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s) {
-    if (g.f.n_chunks * kTM < g.f.D || g.spc <= 0 || g.n_kc * g.spc < g.f.N || g.timeout_ns == 0)
+    if (g.f.n_chunks * kTM < g.f.D || g.spc <= 0 || g.n_kc * g.spc < g.f.N || g.timeout_ns == 0 ||
+        g.n_ct * g.lb < g.f.L)
         return cudaErrorInvalidValue;
     const int P = g.f.M * g.f.M;
     if (!(g.tiles == 1 || g.tiles == 2) || P % g.tiles != 0) return cudaErrorInvalidValue;

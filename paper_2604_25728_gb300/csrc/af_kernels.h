@@ -110,13 +110,15 @@ cudaError_t launch_fwd_dft_f32(const FwdArgs<float2, float>& a, cudaStream_t s);
 cudaError_t launch_fwd_dft_f64(const FwdArgs<double2, double>& a, cudaStream_t s);
 
 // Narrow-window path on tcgen05 tensor cores: one CTA per 128 delays of
-// `tiles` pairs and per column tile of LB bins (LB = gemm_bins_per_tile(L));
+// `tiles` pairs and per column tile of LB bins (LB a power of two in 16..128,
+// at most gemm_bins_per_tile(L));
 // BF16 hi/lo split operands, FP32 accumulation in tensor memory.
 constexpr int kGemmRows = 128;      // delays per tile (MMA M)
 struct GemmArgs {
     FwdArgs<float2, float> f;   // x, h, wmap, mode, pkey/pidx/pchi, cdiag, chi_out, ctr_inc, pdl
     const void* bimg;           // [M][n_ct][n_kc][hi | lo][2 LB x 2 spc] BF16 images of B_m = x_m E
     int* err;                   // bit 1 set when a pipeline wait timed out
+    int lb;                     // bins per column tile (16, 32, 64 or 128)
     int n_ct;                   // column tiles = ceil(L / LB)
     int n_kc;                   // sample chunks = ceil(N / spc)
     int spc;                    // samples per pipeline stage
@@ -126,14 +128,14 @@ struct GemmArgs {
     int test_stall;             // failure-detection test: the MMA issuer waits on a barrier nothing completes
 };
 int gemm_bins_per_tile(int L);
-int gemm_smem_bytes(int L, int N, int spc, int sb, int sa, int tiles);
-bool gemm_shape_supported(int L, int N, int spc, int sb, int sa, int tiles);
-cudaError_t gemm_prepare(int L, int N, int spc, int sb, int sa, int tiles);
+int gemm_smem_bytes(int LB, int N, int spc, int sb, int sa, int tiles);
+bool gemm_shape_supported(int LB, int N, int spc, int sb, int sa, int tiles);
+cudaError_t gemm_prepare(int LB, int N, int spc, int sb, int sa, int tiles);
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
 // B_m = x_m(n) e^{j 2 pi nu_j n} images of one evaluation (E: [N][L] FP32 phasors)
-cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int spc, void* img, int pdl,
-                             cudaStream_t s);
-size_t gemm_bimg_bytes(int M, int N, int L, int spc);
+cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int LB, int spc, void* img,
+                             int pdl, cudaStream_t s);
+size_t gemm_bimg_bytes(int M, int N, int L, int LB, int spc);
 
 // Record the message of a failed call that has no context (read back by
 // af_last_error(NULL) on the same thread).

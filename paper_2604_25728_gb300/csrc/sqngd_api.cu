@@ -65,6 +65,7 @@ struct af_ctx {
     float2* E = nullptr;       // [N][L] e^{j 2 pi nu_j n} (DFT path)
     uint16_t* bimg = nullptr;  // BF16 hi/lo images of B_m = x_m E, rebuilt per evaluation (tensor-core path)
     int gemm_n_ct = 0, gemm_n_kc = 0;
+    int gemm_lb = 0;                      // bins per column tile
     int gemm_spc = 32, gemm_sb = 2, gemm_sa = 2;   // samples per stage, B stages, A stages
     int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
     unsigned long long gemm_timeout_ns = 2000000000ull;   // limit of every pipeline wait
@@ -326,7 +327,27 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         // that nothing completes, with a 50 ms limit
         if (const char* e = getenv("SQNGD_GEMM_TEST_STALL"))
             if (atoi(e) != 0) { c->gemm_test_stall = 1; c->gemm_timeout_ns = 50000000ull; }
-        if (!gemm_shape_supported(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)) {
+        // Column tiles: the widest that covers L, narrowed (down to 16 bins)
+        // while there are fewer tiles than a quarter of the SMs -- every column
+        // tile is an independent part of the output, so narrower tiles add
+        // CTAs without any merge (measured on M=4, N=1024, 128 bins, 101
+        // delays: 128 bins per tile 36.5 us, 64 or 32 bins 29.4 us, 16 bins
+        // 31.5 us per forward pass).
+        {
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1)
+                sms = 1;
+            const int dtiles = (c->D + kGemmRows - 1) / kGemmRows;
+            int lb = gemm_bins_per_tile(L);
+            auto tiles_of = [&](int b) { return P / c->gemm_tiles * dtiles * ((L + b - 1) / b); };
+            while (lb > 16 && 4 * tiles_of(lb) < sms) lb /= 2;
+            if (const char* e = getenv("SQNGD_GEMM_LB")) {
+                const int v = atoi(e);
+                if ((v == 16 || v == 32 || v == 64 || v == 128) && v <= gemm_bins_per_tile(L)) lb = v;
+            }
+            c->gemm_lb = lb;
+        }
+        if (!gemm_shape_supported(c->gemm_lb, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)) {
             c->err = "AF_PATH_SPLIT_BF16: pipeline shape does not fit this N and L";
             return fail(AF_ERR_UNIMPLEMENTED);
         }
@@ -426,8 +447,9 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
         if ((s = upload(c, &c->E, E)) || (s = upload(c, &c->E64, E64))) return fail(s);
     }
     if (c->path == AF_PATH_SPLIT_BF16) {
-        if ((s = dalloc(c, &c->bimg, gemm_bimg_bytes(M, N, L, c->gemm_spc) / sizeof(uint16_t)))) return fail(s);
-        const int LB = gemm_bins_per_tile(L);
+        if ((s = dalloc(c, &c->bimg, gemm_bimg_bytes(M, N, L, c->gemm_lb, c->gemm_spc) / sizeof(uint16_t))))
+            return fail(s);
+        const int LB = c->gemm_lb;
         c->gemm_n_ct = (L + LB - 1) / LB;
         c->gemm_n_kc = (N + c->gemm_spc - 1) / c->gemm_spc;
     }
@@ -481,7 +503,7 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     // kernels' shared-memory limits are raised here, for this geometry, outside any graph capture
     {
         cudaError_t e = (c->path == AF_PATH_FFT) ? fft_prepare_f32(L, N, c->fft_e, c->fft_nt, c->rows_per_chunk)
-                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(L, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)
+                        : (c->path == AF_PATH_SPLIT_BF16) ? gemm_prepare(c->gemm_lb, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, c->gemm_tiles)
                         : dft_prepare_f32(N);
         if (e == cudaSuccess)
             e = c->acc_fft ? fft_prepare_f64(L, N, c->acc_e, 256, c->acc_rows_per_chunk) : dft_prepare_f64(N);
@@ -595,12 +617,14 @@ static FwdArgs<float2, float> fwd_args(af_ctx* c, const float2* x, const float2*
 static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaStream_t s) {
     if (c->path == AF_PATH_SPLIT_BF16) {
         // this evaluation's B_m images, then the contraction
-        cudaError_t e = launch_gemm_bimg(a.x, c->E, c->cfg.M, c->cfg.N, c->cfg.L, c->gemm_spc, c->bimg, a.pdl, s);
+        cudaError_t e = launch_gemm_bimg(a.x, c->E, c->cfg.M, c->cfg.N, c->cfg.L, c->gemm_lb, c->gemm_spc, c->bimg,
+                                         a.pdl, s);
         if (e != cudaSuccess) return e;
         GemmArgs g{};
         g.f = a;
         g.bimg = c->bimg;
         g.err = c->errflag;
+        g.lb = c->gemm_lb;
         g.n_ct = c->gemm_n_ct;
         g.n_kc = c->gemm_n_kc;
         g.spc = c->gemm_spc;

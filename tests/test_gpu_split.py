@@ -189,6 +189,21 @@ def test_split_pipeline_variants(api, orc, shape, monkeypatch):
     _check_terms(orc, ctx, x, h, nu, k_lo, k_hi, 0.2, 1.0)
 
 
+@pytest.mark.parametrize("lb", ["16", "32", "64", "128"])
+def test_split_column_tile_widths(api, orc, lb, monkeypatch):
+    """Every column-tile width (16 to 128 bins per tile; the library narrows
+    the tiles when too few exist to fill the GPU) gives the oracle's chi,
+    terms, cell and gradient on a 128-bin window with a ragged delay tile."""
+    monkeypatch.setenv("SQNGD_GEMM_LB", lb)
+    M, N, nu, k_lo, k_hi = 2, 330, wl.window_grid(0.1, 128), -150, 150
+    x, h = _pair(orc, 800 + int(lb), M, N)
+    ctx = _ctx(api, M, N, 4, nu, k_lo, k_hi, eps=0.2, snrl_db=1.0)
+    chi = ctx.af_ambiguity(_dev(x), _dev(h)).cpu().numpy()
+    ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
+    assert np.max(np.abs(chi - ref)) <= CHI_TOL * np.max(np.abs(ref))
+    _check_terms(orc, ctx, x, h, nu, k_lo, k_hi, 0.2, 1.0)
+
+
 def test_pipeline_wait_timeout_is_reported_and_device_stays_usable(api, orc, monkeypatch):
     """Failure detection without a fault: with the test hook the MMA issuer
     waits on a barrier that nothing completes; the bounded wait (50 ms) gives
