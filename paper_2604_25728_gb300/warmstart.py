@@ -53,10 +53,11 @@ def converge(ctx, b0: np.ndarray, n_outer: int) -> np.ndarray:
     return (st.best_q.cpu().numpy() % ctx.B).astype(np.int32)
 
 
-def generate(n_per_config: int, n_outer: int, seed0: int = 10_000, path=api.AF_PATH_SPLIT_BF16):
-    """Converged designs of the training family: list of (M, N, b0, b_star)."""
+def generate(n_per_config: int, n_outer: int, seed0: int = 10_000, path=api.AF_PATH_SPLIT_BF16, configs=None):
+    """Converged designs of the training family (or of `configs`, a list of
+    (M, N)): list of (M, N, b0, b_star)."""
     data = []
-    for (M, N) in TRAIN_CONFIGS:
+    for (M, N) in (configs or TRAIN_CONFIGS):
         ctx = _ctx(M, N, TRAIN_B, TRAIN_WINDOW, TRAIN_L, TRAIN_KMAX, path)
         for i in range(n_per_config):
             b0 = wl.phase_indices(seed0 + 1000 * M + N + i, M, N, TRAIN_B)
@@ -131,10 +132,11 @@ def load(path: str = DEFAULT_PARAMS):
 
 # ------------------------------------------------------------ time to target
 def _trajectory(ctx, b0, t_max, chunk, stream, stop=None, init_s=0.0):
-    """SQNGD from the code b0 in chunks of `chunk` outer iterations.  After
-    each chunk the current hard design is scored in FP64 (af_eval_hard, not
-    timed).  Returns [(outer iterations, device seconds of the optimiser so
-    far, PSLR dB, max SNRL dB)], stopping early once stop(pslr, snrl) holds."""
+    """SQNGD from the code b0 in chunks of `chunk` outer iterations.  The
+    starting design and, after each chunk, the current hard design are scored
+    in FP64 (af_eval_hard, not timed).  Returns [(outer iterations, device
+    seconds of the optimiser so far, PSLR dB, max SNRL dB)] from iteration 0,
+    stopping early once stop(pslr, snrl) holds."""
     dev = ctx.device
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -145,7 +147,11 @@ def _trajectory(ctx, b0, t_max, chunk, stream, stop=None, init_s=0.0):
     e1.synchronize()
     t = init_s + e0.elapsed_time(e1) / 1e3
     it = 0
-    out = []
+    acc = ctx.af_eval_hard(st.u, st.h)
+    out = [(0, t, float(acc[2]), float(acc[3]))]
+    if stop is not None and stop(acc[2], acc[3]):
+        ctx.af_sync()
+        return out
     while it < t_max:
         e0.record(stream)
         ctx.sqngd_step(st, chunk, log=False)
@@ -161,7 +167,7 @@ def _trajectory(ctx, b0, t_max, chunk, stream, stop=None, init_s=0.0):
     return out
 
 
-def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk: int = 5, log=None):
+def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk: int = 5, log=None, nets=None):
     """Time to a PSL target at equal SNRL on the learned workload (M=4,
     N=1024, B=16, 128 bins on |nu| <= 0.1, |k| <= 50).
 
@@ -171,7 +177,10 @@ def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk:
     An arm reaches the target at the first checkpoint (every `chunk` outer
     iterations) where its current hard design meets both; its time is the
     device time (CUDA events) of the optimiser (and of the warm-start
-    proposal) up to that checkpoint."""
+    proposal) up to that checkpoint.  `nets` maps arm names to further
+    parameter vectors (each becomes a split-BF16 warm-start arm); the record
+    holds every arm's starting PSLR (iteration 0) and, for the networks, the
+    share of the random code's indices their proposals change."""
     w = wl.learned()
     kmax = w.k_hi
     window = float(np.max(np.abs(w.nu)))
@@ -187,7 +196,7 @@ def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk:
     target = max(tr[-1][2] for tr in traj_a.values())
     out["snrl_budget_db"] = snrl_budget
     out["target_pslr_db"] = target
-    out["start_pslr_db"] = [traj_a[s][0][2] for s in seeds]
+    out["start_pslr_db"] = {"random": [traj_a[s][0][2] for s in seeds]}
 
     def ok(pslr, snrl):
         return pslr <= target and snrl <= snrl_budget
@@ -203,10 +212,14 @@ def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk:
         log(f"target {target:.2f} dB at max SNRL <= {snrl_budget:.3f} dB")
     ctx = _ctx(w.M, w.N, w.B, window, w.L, kmax, api.AF_PATH_SPLIT_BF16, w)
     arms["split_random"] = {s: reached(_trajectory(ctx, starts[s], t_max, chunk, stream, ok)) for s in seeds}
+    all_nets = dict(nets or {})
     if params is not None:
+        all_nets = {"split_warmstart": params, **all_nets}
+    out["changed_fraction"] = {}
+    for name, prm in all_nets.items():
         net = api.WarmStart(1, w.N)
-        net.set_params(params)
-        res = {}
+        net.set_params(prm)
+        res, starts_db, changed = {}, [], []
         for s in seeds:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -214,8 +227,13 @@ def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk:
             b_ws = propose(net, starts[s], w.B, window, kmax)
             e1.record(stream)
             e1.synchronize()
-            res[s] = reached(_trajectory(ctx, b_ws, t_max, chunk, stream, ok, e0.elapsed_time(e1) / 1e3))
-        arms["split_warmstart"] = res
+            changed.append(float(np.mean(b_ws != starts[s])))
+            tr = _trajectory(ctx, b_ws, t_max, chunk, stream, ok, e0.elapsed_time(e1) / 1e3)
+            starts_db.append(tr[0][2])
+            res[s] = reached(tr)
+        arms[name] = res
+        out["start_pslr_db"][name] = starts_db
+        out["changed_fraction"][name] = float(np.mean(changed))
         net.close()
     ctx.close()
     for name, res in arms.items():
@@ -226,8 +244,8 @@ def time_to_target(params=None, seeds=(0, 1, 2, 3, 4), t_max: int = 2000, chunk:
                      "per_seed_s": [None if t is None else float(t) for _, t in res.values()],
                      "per_seed_outer": [it for it, _ in res.values()]}
     base = out["fp32_random"]["median_s"]
-    for name in ("split_random", "split_warmstart"):
-        if name in out and out[name]["median_s"] and base:
+    for name in arms:
+        if name != "fp32_random" and out[name]["median_s"] and base:
             out[name]["speedup_vs_fp32_random"] = base / out[name]["median_s"]
     return out
 
@@ -244,6 +262,16 @@ def main(argv=None):
     r = sub.add_parser("ttt", help="time to PSL target with the saved network")
     r.add_argument("--params", default=DEFAULT_PARAMS)
     r.add_argument("--t-max", type=int, default=2000)
+    st = sub.add_parser("study", help="time to PSL target over more seeds with a check every outer iteration, "
+                                      "optionally with a second network trained at the evaluated size")
+    st.add_argument("--params", default=DEFAULT_PARAMS)
+    st.add_argument("--seeds", type=int, default=10)
+    st.add_argument("--chunk", type=int, default=1)
+    st.add_argument("--t-max", type=int, default=2000)
+    st.add_argument("--train-at-size", type=int, default=0,
+                    help="designs to generate at the evaluated size (M=4, N=1024) for a second network (0: none)")
+    st.add_argument("--outer", type=int, default=800)
+    st.add_argument("--out", default="")
     a = p.parse_args(argv)
     torch.cuda.set_device(0)
     if a.cmd == "train":
@@ -264,6 +292,26 @@ def main(argv=None):
                "generate_s": t1 - t0, "train_s": time.time() - t1}
         save(a.out, params, rec)
         print(json.dumps({k: v for k, v in rec.items() if k != "loss_history"}))
+    elif a.cmd == "study":
+        params, rec = load(a.params)
+        nets, extra = {}, {}
+        if a.train_at_size > 0:
+            w = wl.learned()
+            t0 = time.time()
+            data = generate(a.train_at_size, a.outer, seed0=50_000, configs=[(w.M, w.N)])
+            t1 = time.time()
+            net, hist = train(data, epochs=30, lr=2e-3, log=print)
+            nets["split_warmstart_at_size"] = net.get_params()
+            extra = {"designs": len(data), "outer_iterations": a.outer, "generate_s": t1 - t0,
+                     "train_s": time.time() - t1, "final_loss": hist[-1]}
+            net.close()
+        res = time_to_target(params, seeds=tuple(range(a.seeds)), t_max=a.t_max, chunk=a.chunk, log=print, nets=nets)
+        res["network_at_size"] = extra
+        txt = json.dumps(res)
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(txt)
+        print(txt)
     else:
         params, rec = load(a.params)
         print(json.dumps(time_to_target(params, t_max=a.t_max, log=print)))
