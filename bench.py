@@ -121,30 +121,45 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.lines = []
         self.thread = None
+        self.first = threading.Event()
+        self.start_at = 0
 
-    def start(self):
+    def start(self, wait_s: float = 5.0):
+        """Start sampling; return once the first sample has arrived (nvidia-smi
+        takes a few hundred ms to start), so that the timed region after it is
+        covered."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        self.first.wait(wait_s)
+
+    def mark(self):
+        """The timed region starts here: only later samples are reported."""
+        self.start_at = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_end = time.time() + 1.0        # a region shorter than the period: wait for the next sample
+        while len(self.lines) <= self.start_at and time.time() < t_end:
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -154,7 +169,7 @@ class ClockSampler:
             self.thread.join(timeout=5)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in self.lines[self.start_at:]:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -451,6 +466,7 @@ def run_ours(args):
     sampler.start()
     barrier()
     torch.cuda.synchronize()
+    sampler.mark()
     for i in range(K):
         ev0[i].record(stream)
         ctx.sqngd_step(st, 1, log=False)

@@ -122,3 +122,26 @@ def test_adjoint_flops_by_enumeration():
     rows = w.M * w.D
     exp = rows * (2 * 5 * w.L * math.log2(w.L) + 6 * w.L) + 22 * valid * rows / w.D
     assert abs(bench._adj_flops(w, rows) - exp) < 1e-9 * exp
+
+
+def test_clock_samples_before_the_timed_region_are_dropped():
+    """Only samples taken after mark() count; throttle reasons are read from
+    the Active columns."""
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc = _Proc()
+    idle = "0, 345, 2070, 100.0, 0x1, Not Active, Not Active, Not Active, Not Active"
+    busy = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active"
+    s.lines = [idle, idle]
+    s.mark()
+    s.lines += [busy, busy, capped]
+    r = s.stop()
+    assert r["samples"] == 3 and r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"]
