@@ -135,22 +135,53 @@ __device__ __forceinline__ constexpr double w32s(int s) {
          : s == 11 ? 0.831469612302545237079 : s == 13 ? 0.555570233019602224743 : 0.195090322016128267848;
 }
 
-// Multiply o by e^{+j 2 pi s / R} (s < R/2, R <= 32), folding the trivial cases.
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// One radix-2 butterfly with a compile-time twiddle, tp = e + w o and
+// tm = e - w o for w = e^{+j 2 pi S / R}, with the multiplications folded into
+// fused multiply-adds: six operations where a complex multiply and two
+// complex additions take eight.  A general w = (c, s) is applied as
+// c (o.x - t o.y, o.y + t o.x) with t = s/c when |c| >= |s|, else as
+// s (u o.x - o.y, o.x + u o.y) with u = c/s (the tangent form of the
+// rotation), so neither ratio exceeds 1.
 template <int R, int S, typename C>
-__device__ __forceinline__ C twiddle_const(C o) {
+__device__ __forceinline__ void bfly_const(C e, C o, C& tp, C& tm) {
     using T = decltype(o.x);
     constexpr int s32 = S * (32 / R);
-    if constexpr (s32 == 0) return o;
-    else if constexpr (s32 == 8) return cmulj(o);
-    else if constexpr (s32 == 4 || s32 == 12) {
+    if constexpr (s32 == 0) {
+        tp = cadd(e, o);
+        tm = csub(e, o);
+    } else if constexpr (s32 == 8) {            // w = j: w o = (-o.y, o.x)
+        tp = mk(e.x - o.y, e.y + o.x);
+        tm = mk(e.x + o.y, e.y - o.x);
+    } else if constexpr (s32 == 4 || s32 == 12) {
         constexpr T r2 = (T)0.70710678118654752440;
-        // e^{j pi/4} = r2 (1 + j); e^{j 3pi/4} = r2 (-1 + j)
-        if constexpr (s32 == 4) return mk((o.x - o.y) * r2, (o.x + o.y) * r2);
-        else return mk((-o.x - o.y) * r2, (o.x - o.y) * r2);
-    } else if constexpr ((s32 & 1) == 0) {
-        return cmul(o, mk((T)w16c(s32 / 2), (T)w16s(s32 / 2)));
+        const T d = o.x - o.y, u = o.x + o.y;
+        if constexpr (s32 == 4) {               // w o = r2 (o.x - o.y, o.x + o.y)
+            tp = mk(fmadd(r2, d, e.x), fmadd(r2, u, e.y));
+            tm = mk(fmadd(-r2, d, e.x), fmadd(-r2, u, e.y));
+        } else {                                // w o = r2 (-(o.x + o.y), o.x - o.y)
+            tp = mk(fmadd(-r2, u, e.x), fmadd(r2, d, e.y));
+            tm = mk(fmadd(r2, u, e.x), fmadd(-r2, d, e.y));
+        }
     } else {
-        return cmul(o, mk((T)w32c(s32), (T)w32s(s32)));
+        constexpr double cw = (s32 & 1) ? w32c(s32) : w16c(s32 / 2);
+        constexpr double sw = (s32 & 1) ? w32s(s32) : w16s(s32 / 2);
+        constexpr bool by_cos = (cw >= 0 ? cw : -cw) >= (sw >= 0 ? sw : -sw);
+        T a, b;
+        constexpr T f = (T)(by_cos ? cw : sw);
+        if constexpr (by_cos) {
+            constexpr T t = (T)(sw / cw);
+            a = fmadd(-t, o.y, o.x);
+            b = fmadd(t, o.x, o.y);
+        } else {
+            constexpr T u = (T)(cw / sw);
+            a = fmadd(u, o.x, -o.y);
+            b = fmadd(u, o.y, o.x);
+        }
+        tp = mk(fmadd(f, a, e.x), fmadd(f, b, e.y));
+        tm = mk(fmadd(-f, a, e.x), fmadd(-f, b, e.y));
     }
 }
 
@@ -170,10 +201,7 @@ template <int R, int ST> struct Dft {
     template <int S, typename C>
     static __device__ __forceinline__ void combine(const C* v, C* t) {
         if constexpr (S < R / 2) {
-            C e = v[2 * ST * S];
-            C o = twiddle_const<R, S>(v[ST + 2 * ST * S]);
-            t[S] = cadd(e, o);
-            t[S + R / 2] = csub(e, o);
+            bfly_const<R, S>(v[2 * ST * S], v[ST + 2 * ST * S], t[S], t[S + R / 2]);
             combine<S + 1>(v, t);
         }
     }
