@@ -71,7 +71,22 @@ __device__ __forceinline__ int count_lt(const QuantArgs& q, float v) {
 // nearest z (where tanh is not saturated and the recursion has taken no
 // steps), each e_i by one multiply; the terms far from z, where the
 // accumulated rounding of the recursion grows, are saturated.
+//
+// When the tanh width 1/c spans at least four threshold spacings (alpha =
+// 2c/K <= 1/2, which holds at K = B r_n = 1600 or 6400 with c = 300) the
+// uniform sum has a closed form instead, soft_q_closed below, which costs the
+// same at any K.
+__device__ __forceinline__ void soft_q_closed(const QuantArgs& q, float z, float* y, float* dydz, float2* x);
+
+__device__ __forceinline__ bool soft_q_closed_ok(const QuantArgs& q) {
+    return q.uniform && 4.f * q.c <= (float)q.K;     // alpha = 2c/K <= 1/2
+}
+
 __device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, float* dydz, float2* x) {
+    if (soft_q_closed_ok(q)) {
+        soft_q_closed(q, z, y, dydz, x);
+        return;
+    }
     int i0, i1;
     if (q.uniform) {
         // The window's edges need no exact count: a threshold misplaced across
@@ -135,6 +150,58 @@ __device__ __forceinline__ void soft_q(const QuantArgs& q, float z, float* y, fl
     if (x) {
         // phase in cycles: i0/B + s, reduced modulo 1 before sincospi
         float f = (float)(i0 % q.B) / (float)q.B + s;
+        f -= floorf(f);
+        float sn, cs;
+        sincospif(2.f * f, &sn, &cs);
+        *x = make_float2(cs, sn);
+    }
+}
+
+// Closed form of Eq. 24 for the uniform thresholds rho_i = (i + 1/2)/K with
+// a_i = a.  With tanh(u) + 1 = 2 s(2u) (s the logistic function) the sum is
+// y(z) = 2a S(z), S(z) = sum_{i<K} s(alpha (x - i)), alpha = 2c/K, x = zK - 1/2:
+// a sum of a smooth function at unit spacing.  The midpoint Euler-Maclaurin
+// formula over [-1/2, K - 1/2] turns it into the integral plus end terms:
+//   S = zK + [sp(-v0) - sp(v1)]/alpha + (alpha/24)[d1(v1) - d1(v0)]
+//         - (7 alpha^3/5760)[d3(v1) - d3(v0)] + R,
+// with v0 = 2cz and v1 = 2c(z - 1) the arguments at the two ends, sp the
+// softplus log(1 + e^v) (the integral of s), and d1 = s(1 - s), d3 =
+// d1 (1 - 6 d1) its first and third derivatives.  The summand is analytic in
+// a strip of half-width pi/alpha, so the error of the midpoint rule over the
+// whole line is of order e^{-2 pi^2/alpha} (e^{-52} at alpha = 3/8), and the
+// next end term is below 1e-7 for alpha <= 1/2: both far below FP32
+// resolution.  Its derivative gives Q_A'(z) = 2a dS/dz:
+//   dS/dz = K[s(v0) - s(v1)] + 2c (alpha/24)[d2(v1) - d2(v0)]
+//         - 2c (7 alpha^3/5760)[d4(v1) - d4(v0)],
+// d2 = d1 (1 - 2s) and d4 = d1 (1 - 2s)(1 - 12 d1) the second and fourth
+// derivatives.  y = 2aK z + 2a (S - zK): the first product is split exactly
+// (hi + lo by a fused multiply-add), so that the phase y mod 1 keeps the
+// precision of the small remainder instead of that of y (up to r_n).
+__device__ __forceinline__ void soft_q_closed(const QuantArgs& q, float z, float* y, float* dydz, float2* x) {
+    const float K = (float)q.K, c = q.c, a2 = 2.f * q.a;
+    const float al = 2.f * c / K;
+    const float v0 = 2.f * c * z, v1 = 2.f * c * (z - 1.f);
+    const float e0 = expf(-fabsf(v0)), e1 = expf(-fabsf(v1));
+    const float sp0 = fmaxf(-v0, 0.f) + log1pf(e0);          // sp(-v0)
+    const float sp1 = fmaxf(v1, 0.f) + log1pf(e1);           // sp(v1)
+    const float r0 = 1.f / (1.f + e0), r1 = 1.f / (1.f + e1);
+    const float s0 = (v0 >= 0.f) ? r0 : e0 * r0;             // s(v0)
+    const float s1 = (v1 >= 0.f) ? r1 : e1 * r1;             // s(v1)
+    const float t0 = e0 * r0 * r0, t1 = e1 * r1 * r1;       // d1(v0), d1(v1): e^{-|v|}/(1 + e^{-|v|})^2
+    const float k1 = al * (1.f / 24.f), k3 = al * al * al * (7.f / 5760.f);
+    const float rem = (sp0 - sp1) / al + k1 * (t1 - t0) - k3 * (t1 * (1.f - 6.f * t1) - t0 * (1.f - 6.f * t0));
+    const float P = a2 * K;
+    const float hi = P * z;
+    const float r = fmaf(P, z, -hi) + a2 * rem;
+    if (y) *y = hi + r;
+    if (dydz) {
+        const float g0 = t0 * (1.f - 2.f * s0), g1 = t1 * (1.f - 2.f * s1);
+        const float dS = K * (s0 - s1) + 2.f * c * (k1 * (g1 - g0) -
+                         k3 * (g1 * (1.f - 12.f * t1) - g0 * (1.f - 12.f * t0)));
+        *dydz = a2 * dS;
+    }
+    if (x) {
+        float f = (hi - floorf(hi)) + r;
         f -= floorf(f);
         float sn, cs;
         sincospif(2.f * f, &sn, &cs);

@@ -268,11 +268,21 @@ def test_quantize_bit_exact(api, orc, B, r_n):
     np.testing.assert_allclose(x.cpu().numpy(), np.exp(2j * np.pi * ob / B), atol=2e-7)
 
 
-def test_soft_quantize_matches_oracle(api, orc):
-    B, r_n, c = 16, 100, 300.0
+@pytest.mark.parametrize("B,r_n,c", [
+    (16, 100, 300.0),    # K = 1600: closed form (alpha = 2c/K = 3/8)
+    (64, 100, 300.0),    # K = 6400: closed form (alpha = 3/32)
+    (8, 100, 100.0),     # closed form at alpha = 1/4
+    (4, 100, 300.0),     # alpha = 3/2: the windowed sum
+    (8, 100, 300.0),     # alpha = 3/4: the windowed sum
+])
+def test_soft_quantize_matches_oracle(api, orc, B, r_n, c):
+    """Eq. 24 against the oracle's sum of all K terms, on random z and on the
+    ends of [0, 1] where the sum is not saturated on one side."""
     rho, a = orc.thresholds(B, r_n)
     rho32 = rho.astype(np.float32).astype(np.float64)
-    z = wl.uniform(21, 5000, 2).astype(np.float32)
+    u = wl.uniform(21, 5000, 2)
+    z = np.concatenate([u[:4000], 0.03 * u[4000:4500], 1.0 - 0.03 * u[4500:], [0.0, 1.0, 1e-6, 1.0 - 1e-6]])
+    z = z.astype(np.float32)
     ctx = _ctx(api, 1, 8, B, wl.full_grid(32), -7, 7, r_n=r_n, c=c)
     y, dy, x = ctx.soft_quantize(_dev(z))
     ctx.af_sync()
