@@ -30,6 +30,8 @@
 // timeout sets bit 1 of the error flag and ends the kernel cleanly.
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "af_common.cuh"
 #include "af_kernels.h"
 #include "af_tc.cuh"
@@ -119,10 +121,19 @@ __host__ __device__ constexpr int gemm_tmem_cols(int NC, int SPC, int SA, int T)
          : (T * NC + 2 * SPC * SA * T <= 512) ? 512 : 0;
 }
 
+// One piece of a CTA's work: chunks ib .. ib + nch - 1 of tile q (pair group
+// pg, column tile ct, delay block blk), whose window starts at chunk c0 of the
+// samples.  whole: the piece is the whole tile; else it is piece `piece` of
+// the `npieces` CTAs that share the tile.
+struct GSeg {
+    int q, pg, ct, blk, c0, ib, nch, piece, npieces, whole;
+};
+
 // kSB stages of B images in shared memory (filled by bulk copies), kSA
-// stages of lag products in tensor memory (filled by tcgen05.st); chunk i
-// uses B stage i % kSB and A stage i % kSA.
-template <int NC, int kSPC, int kSB, int kSA, int T>
+// stages of lag products in tensor memory (filled by tcgen05.st); the CTA's
+// chunk g (counted over all its pieces) uses B stage g % kSB and A stage
+// g % kSA.
+template <int NC, int kSPC, int kSB, int kSA, int T, bool SPLIT>
 __global__ void __launch_bounds__(32 * (4 * T + 2), 1)
 fwd_gemm_kernel(const GemmArgs g) {
     const FwdArgs<float2, float>& a = g.f;
@@ -134,6 +145,7 @@ fwd_gemm_kernel(const GemmArgs g) {
     constexpr int TCOLS = gemm_tmem_cols(NC, kSPC, kSA, T);
     static_assert(NC % 32 == 0 && NC >= 32 && NC <= 256, "column tile");
     static_assert(TCOLS > 0 && kSPC % 8 == 0, "stage shape");
+    static_assert(!SPLIT || T == 1, "the split schedule takes one pair per CTA");
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* bst = smem_raw;                                        // [kSB][STAGE_BYTES]
@@ -147,26 +159,16 @@ fwd_gemm_kernel(const GemmArgs g) {
     __shared__ long long ri[T][4];
     __shared__ float2 rc[T][4];
     __shared__ DFloat red[T][2][4];
+    __shared__ GSeg s_seg[kGemmMaxSeg];
+    __shared__ int s_nseg, s_ticket;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    // CTAs are ordered pair-group-fastest: consecutive CTAs share the delay
-    // block and column tile -- hence every B image, which they read from L2.
-    // A CTA owns the T consecutive pairs pg*T .. pg*T + T-1 of one delay block.
     const int bx = blockIdx.x;
     const int P = a.M * a.M;
     const int PG = P / T;
-    const int pg = bx % PG;
-    const int rest = bx / PG;
-    const int ct = rest % g.n_ct;
-    const int tile = rest / g.n_ct;
+    const int PGC = PG * g.n_ct;
     const int N = a.N, L = a.L, D = a.D;
-    const int d0 = tile * kTM;
-    const int k_first = a.k_lo + d0;
-    const int k_last = a.k_lo + min(D, d0 + kTM) - 1;
-    const int n_begin = max(0, -k_last), n_end = min(N, N - k_first);
-    const int c0 = n_begin / kSPC;
-    const int nch = (n_end + kSPC - 1) / kSPC - c0;
 
     if (tid == 0) {
         for (int s = 0; s < kSB; ++s) {
@@ -181,6 +183,53 @@ fwd_gemm_kernel(const GemmArgs g) {
         tc::mbar_init(&never, 1);          // nothing arrives here (failure-detection test)
         s_abort = 0;
         tc::mbar_fence_init();
+        // This CTA's pieces of work.  Tiles are ordered pair-group-fastest:
+        // consecutive tiles share the delay block and column tile -- hence every
+        // B image, which their CTAs read from L2.
+        int ns = 0;
+        if constexpr (!SPLIT) {
+            GSeg sg;
+            sg.q = bx;
+            sg.pg = bx % PG;
+            sg.ct = (bx / PG) % g.n_ct;
+            sg.blk = bx / PGC;
+            sg.nch = gemm_block_chunks(a.k_lo, D, N, kSPC, sg.blk, &sg.c0);
+            sg.ib = 0; sg.piece = 0; sg.npieces = 1; sg.whole = 1;
+            s_seg[ns++] = sg;
+        } else {
+            // chunks [w0, w1) of all tiles' chunks in tile order
+            const long long W = g.split_work, G = g.split_ctas;
+            const long long w0 = (long long)bx * W / G, w1 = (long long)(bx + 1) * W / G;
+            long long base = 0;                       // first chunk of block b
+            int b = 0, c0b = 0;
+            int nb = gemm_block_chunks(a.k_lo, D, N, kSPC, 0, &c0b);
+            for (long long x = w0; x < w1 && ns < kGemmMaxSeg;) {
+                while (x >= base + (long long)PGC * nb) {
+                    base += (long long)PGC * nb;
+                    ++b;
+                    nb = gemm_block_chunks(a.k_lo, D, N, kSPC, b, &c0b);
+                }
+                const int qi = (int)((x - base) / nb);        // tile within the block
+                const long long ts = base + (long long)qi * nb, te = ts + nb;
+                const long long xe = w1 < te ? w1 : te;
+                GSeg sg;
+                sg.q = b * PGC + qi;
+                sg.pg = qi % PG;
+                sg.ct = qi / PG;
+                sg.blk = b;
+                sg.c0 = c0b;
+                sg.ib = (int)(x - ts);
+                sg.nch = (int)(xe - x);
+                // the CTAs holding the tile's first and last chunks
+                const long long cf = ((ts + 1) * G - 1) / W, cl = (te * G - 1) / W;
+                sg.piece = (int)(bx - cf);
+                sg.npieces = (int)(cl - cf + 1);
+                sg.whole = sg.npieces == 1;
+                s_seg[ns++] = sg;
+                x = xe;
+            }
+        }
+        s_nseg = ns;
     }
     if (warp == WMMA) {
         __syncwarp();
@@ -191,42 +240,45 @@ fwd_gemm_kernel(const GemmArgs g) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = s_tmem;
+    const int nseg = SPLIT ? s_nseg : 1;
     volatile int* abort_flag = &s_abort;
-
-    // the T pairs of a CTA share their transmit waveform (T divides M), so one B_m image
-    const int m_cta = (pg * T) / a.M;
-    const unsigned char* img = reinterpret_cast<const unsigned char*>(g.bimg) +
-                               (((size_t)m_cta * g.n_ct + ct) * g.n_kc + c0) * (size_t)STAGE_BYTES;
+    int total = 0;                                    // chunks of this CTA
+    for (int k = 0; k < nseg; ++k) total += s_seg[k].nch;
 
     if (warp == WLOAD) {
         // ---------------------------------------------------- B loader --
-        // Stage s of chunk i: one bulk copy of the whole stage, completing on bfull[s].
-        auto issue = [&](int i, int s) {
-            tc::mbar_arrive_expect_tx(&bfull[s], STAGE_BYTES);
-            tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
-        };
+        // Stage s of chunk g: one bulk copy of the whole stage, completing on bfull[s].
+        // The T pairs of a CTA share their transmit waveform (T divides M), so one B_m image.
         int issued = 0;
         // the B_m images are written by the kernel just ahead in the stream
         pdl_wait();
         pdl_trigger();
         if (lane == 0) {
-            const int pro = min(kSB, nch);
-            for (int i = 0; i < pro; ++i) issue(i, i);
-            issued = pro;
-        }
-        if (lane == 0) {
-            for (int i = kSB; i < nch; ++i) {
-                const int s = i % kSB;
-                // the MMAs have finished with stage s
-                if (!gwait(&bempty[s], ((i / kSB) - 1) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
-                issue(i, s);
-                issued = i + 1;
+            bool okl = true;
+            int gi = 0;
+            for (int k = 0; okl && k < nseg; ++k) {
+                const GSeg sg = s_seg[k];
+                const int m_cta = (sg.pg * T) / a.M;
+                const unsigned char* img = reinterpret_cast<const unsigned char*>(g.bimg) +
+                    (((size_t)m_cta * g.n_ct + sg.ct) * g.n_kc + sg.c0 + sg.ib) * (size_t)STAGE_BYTES;
+                for (int i = 0; i < sg.nch; ++i, ++gi) {
+                    const int s = gi % kSB;
+                    // the MMAs have finished with stage s
+                    if (gi >= kSB &&
+                        !gwait(&bempty[s], ((gi / kSB) - 1) & 1, abort_flag, g.err, false, g.timeout_ns)) {
+                        okl = false;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&bfull[s], STAGE_BYTES);
+                    tc::bulk_g2s(bst + s * STAGE_BYTES, img + (size_t)i * STAGE_BYTES, STAGE_BYTES, &bfull[s]);
+                    issued = gi + 1;
+                }
             }
             // every stage in flight has landed, and every MMA commit has
             // arrived, before the CTA exits
             for (int i = max(0, issued - kSB); i < issued; ++i)
                 gwait(&bfull[i % kSB], (i / kSB) & 1, abort_flag, g.err, true, g.timeout_ns);
-            for (int i = max(0, nch - kSB); i < nch; ++i)
+            for (int i = max(0, total - kSB); i < total; ++i)
                 gwait(&bempty[i % kSB], (i / kSB) & 1, abort_flag, g.err, true, g.timeout_ns);
         }
     } else if (warp == WMMA) {
@@ -244,30 +296,40 @@ fwd_gemm_kernel(const GemmArgs g) {
             bool go = true;
             if (g.test_stall) go = gwait(&never, 0, abort_flag, g.err, false, g.timeout_ns);
             constexpr uint64_t kStageStep = STAGE_BYTES >> 4, kLoStep = (NC * kKC * 2) >> 4, kKStep = 256 >> 4;
-            for (int i = 0; go && i < nch; ++i) {
-                const int s = i % kSB, sa = i % kSA;
-                if (!gwait(&bfull[s], (i / kSB) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
-                if (!gwait(&afull[sa], (i / kSA) & 1, abort_flag, g.err, false, g.timeout_ns)) break;
-                tc::fence_after_sync();
-                const uint64_t dh = dbase + (uint64_t)s * kStageStep;
-                const uint64_t dl = dh + kLoStep;
-                const uint32_t acc0 = (i > 0) ? 1u : 0u;
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    const uint32_t d_t = tbase + t * NC;
-                    const uint32_t a_hi = tbase + T * NC + (sa * T + t) * kKC;
-#pragma unroll
-                    for (int q = 0; q < kKC / 16; ++q) {
-                        mma_ts(d_t, a_hi + 8 * q, dh + q * kKStep, idesc, q == 0 ? acc0 : 1u);
-                        mma_ts(d_t, a_hi + 8 * q, dl + q * kKStep, idesc, 1u);
-                        mma_ts(d_t, a_hi + kSPC + 8 * q, dh + q * kKStep, idesc, 1u);
+            int gi = 0, commits = 0;
+            for (int k = 0; go && k < nseg; ++k) {
+                const int nchk = s_seg[k].nch;
+                for (int i = 0; i < nchk; ++i, ++gi) {
+                    const int s = gi % kSB, sa = gi % kSA;
+                    if (!gwait(&bfull[s], (gi / kSB) & 1, abort_flag, g.err, false, g.timeout_ns) ||
+                        !gwait(&afull[sa], (gi / kSA) & 1, abort_flag, g.err, false, g.timeout_ns)) {
+                        go = false;
+                        break;
                     }
+                    tc::fence_after_sync();
+                    const uint64_t dh = dbase + (uint64_t)s * kStageStep;
+                    const uint64_t dl = dh + kLoStep;
+                    const uint32_t acc0 = (i > 0) ? 1u : 0u;    // each piece starts a fresh accumulator
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        const uint32_t d_t = tbase + t * NC;
+                        const uint32_t a_hi = tbase + T * NC + (sa * T + t) * kKC;
+#pragma unroll
+                        for (int q = 0; q < kKC / 16; ++q) {
+                            mma_ts(d_t, a_hi + 8 * q, dh + q * kKStep, idesc, q == 0 ? acc0 : 1u);
+                            mma_ts(d_t, a_hi + 8 * q, dl + q * kKStep, idesc, 1u);
+                            mma_ts(d_t, a_hi + kSPC + 8 * q, dh + q * kKStep, idesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&bempty[s]);
+                    tc::mma_commit(&aempty[sa]);
                 }
-                tc::mma_commit(&bempty[s]);
-                tc::mma_commit(&aempty[sa]);
+                // the piece's accumulator is complete (after an abort: every
+                // MMA issued so far has finished)
+                tc::mma_commit(&accfull);
+                ++commits;
             }
-            tc::mma_commit(&accfull);
-            gwait(&accfull, 0, abort_flag, g.err, true, g.timeout_ns);
+            if (commits > 0) gwait(&accfull, (commits - 1) & 1, abort_flag, g.err, true, g.timeout_ns);
         }
     } else {
         // ------------------------------------ producers and epilogue --
@@ -275,13 +337,24 @@ fwd_gemm_kernel(const GemmArgs g) {
         pdl_trigger();
         if (a.ctr_inc != nullptr && bx == 0 && tid == 0) a.ctr_inc[0] += 1;
         const int t = tid / kTM, r = tid % kTM;          // this thread's tile and row
-        const int pair = pg * T + t;
-        const int m = pair / a.M, l = pair - m * a.M;
-        const int ob = (pair * a.n_chunks + tile) * g.n_ct + ct;   // partial record (pair-major)
+        const int wq = warp & 3;                          // lane quarter of tensor memory
+        const uint32_t trow = tbase + ((uint32_t)(wq * 32) << 16);
         uint2* hs = xh_base + t * XH;                    // [kSPC * n_kc + kTM] split conj(h_l) window
+        bool ok = true;
+        int gi = 0;
+        for (int k = 0; k < nseg; ++k) {
+        const GSeg sg = s_seg[k];
+        const int pair = sg.pg * T + t;
+        const int m = pair / a.M, l = pair - m * a.M;
+        const int ob = (pair * a.n_chunks + sg.blk) * g.n_ct + sg.ct;   // partial record (pair-major)
+        const int d0 = sg.blk * kTM;
+        const int k_first = a.k_lo + d0;
+        const int c0 = sg.c0 + sg.ib, nch = sg.nch;
         const float2* xm = a.x + (size_t)m * N;
         const float2* hl = a.h + (size_t)l * N;
         const int nh = kSPC * nch + kTM;
+        // the previous piece's copies have read the window
+        if (k > 0) asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
         // the window conj(h_l(p)), p = SPC c0 + k_first + i, split once into
         // BF16 (re, im) hi and lo pairs: all loads of a batch are in flight
         // before the first store
@@ -303,8 +376,9 @@ fwd_gemm_kernel(const GemmArgs g) {
             }
         }
         // chi_mm(0, 0) = sum_n x_m(n) conj(h_m(n)) (SNRL, Eq. 38) while the first
-        // B stages are still in flight: exact products, double-float partials and tree
-        if (a.cdiag != nullptr && tile == 0 && ct == 0) {
+        // B stages are still in flight, by the CTA holding the first chunk of
+        // delay block 0: exact products, double-float partials and tree
+        if (a.cdiag != nullptr && sg.blk == 0 && sg.ct == 0 && sg.ib == 0) {
             const bool diag = (m == l);
             DFloat sr = {0.f, 0.f}, si = {0.f, 0.f};
             if (diag) {
@@ -331,19 +405,17 @@ fwd_gemm_kernel(const GemmArgs g) {
         }
         asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
 
-        const int wq = warp & 3;                          // lane quarter of tensor memory
-        const uint32_t trow = tbase + ((uint32_t)(wq * 32) << 16);
-        bool ok = true;
-        for (int i = 0; i < nch; ++i) {
-            const int s = i % kSA;
-            if (i >= kSA) {
+        for (int i = 0; i < nch; ++i, ++gi) {
+            const int s = gi % kSA;
+            if (ok && gi >= kSA) {
                 // one lane polls; the warp takes its verdict before the
                 // aligned tensor-memory stores
                 bool w = true;
-                if (lane == 0) w = gwait(&aempty[s], ((i / kSA) - 1) & 1, abort_flag, g.err, false, g.timeout_ns);
-                if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
+                if (lane == 0) w = gwait(&aempty[s], ((gi / kSA) - 1) & 1, abort_flag, g.err, false, g.timeout_ns);
+                if (!__shfl_sync(0xffffffffu, w, 0)) ok = false;
                 tc::fence_after_sync();
             }
+            if (!ok) continue;
             // row r, sample n = SPC (c0 + i) + u: conj(h_l(n + k)) = hs[SPC i + r + u]
             uint32_t hi[kSPC], lo[kSPC];
             const uint2* hc = hs + i * kSPC + r;
@@ -368,12 +440,39 @@ fwd_gemm_kernel(const GemmArgs g) {
         long long best_idx = 0x7fffffffffffffffLL;
         float2 best_c = make_float2(0.f, 0.f);
         bool acc_ready = ok;
-        if (lane == 0 && ok) acc_ready = gwait(&accfull, 0, abort_flag, g.err, false, g.timeout_ns);
-        if (__shfl_sync(0xffffffffu, acc_ready, 0)) {
-            tc::fence_after_sync();
+        if (lane == 0 && ok) acc_ready = gwait(&accfull, k & 1, abort_flag, g.err, false, g.timeout_ns);
+        acc_ready = __shfl_sync(0xffffffffu, acc_ready, 0);
+        if (acc_ready) tc::fence_after_sync();
+        // A shared tile: every piece stores its partial ([column][row], so a
+        // warp's stores are contiguous) and takes a ticket; the last piece to
+        // arrive adds all partials in piece order (the same sum whichever CTA
+        // is last) and finishes the tile.  No CTA waits for another.
+        bool finish = true;
+        const size_t pstride = (size_t)NC * kTM;
+        const float* tile_part = SPLIT ? g.part + (size_t)sg.q * g.max_pieces * pstride : nullptr;
+        if (SPLIT && !sg.whole) {
+            if (acc_ready) {
+                float* mine = g.part + ((size_t)sg.q * g.max_pieces + sg.piece) * pstride + r;
+#pragma unroll 1
+                for (int cc = 0; cc < NC / 32; ++cc) {
+                    float v[32];
+                    tc::tmem_ld32(trow + t * NC + cc * 32, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int b = 0; b < 32; ++b) __stcg(mine + (size_t)(cc * 32 + b) * kTM, v[b]);
+                }
+                __threadfence();
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+            if (tid == 0) s_ticket = atomicAdd(g.tile_cnt + sg.q, 1);
+            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+            finish = s_ticket == sg.npieces - 1;
+            if (finish) __threadfence();
+        }
+        if (finish && acc_ready) {
             const int d = d0 + r;
-            const int k = a.k_lo + d;
-            const bool row_ok = d < D && !(m == l && k == 0);
+            const int kd = a.k_lo + d;
+            const bool row_ok = d < D && !(m == l && kd == 0);
             const bool dump = a.mode == FWD_DUMP;
             const bool fast = !dump && a.weight_mode == WM_UNIFORM;
 #pragma unroll 1
@@ -381,12 +480,29 @@ fwd_gemm_kernel(const GemmArgs g) {
                 float v[32];
                 tc::tmem_ld32(trow + t * NC + cc * 32, v);
                 tc::tmem_ld_wait();
+                if (SPLIT && !sg.whole) {
+                    float acc[32];
+#pragma unroll
+                    for (int b = 0; b < 32; ++b) acc[b] = 0.f;
+                    for (int pc = 0; pc < sg.npieces; ++pc) {
+                        if (pc == sg.piece) {
+#pragma unroll
+                            for (int b = 0; b < 32; ++b) acc[b] += v[b];
+                        } else {
+                            const float* src = tile_part + pc * pstride + (size_t)(cc * 32) * kTM + r;
+#pragma unroll
+                            for (int b = 0; b < 32; ++b) acc[b] += __ldcg(src + (size_t)b * kTM);
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < 32; ++b) v[b] = acc[b];
+                }
                 if (fast) {
                     // cells of a row are visited in increasing index order, so
                     // a group only matters if its largest key beats the best so
                     // far, and then its first maximal cell is the candidate
                     float key[16];
-                    const int jb = ct * LB + cc * 16;
+                    const int jb = sg.ct * LB + cc * 16;
 #pragma unroll
                     for (int b = 0; b < 16; ++b)
                         key[b] = (row_ok && jb + b < L) ? fmaf(v[2 * b], v[2 * b], v[2 * b + 1] * v[2 * b + 1]) : -1.f;
@@ -407,7 +523,7 @@ fwd_gemm_kernel(const GemmArgs g) {
                 }
 #pragma unroll
                 for (int b = 0; b < 16; ++b) {
-                    const int jj = ct * LB + cc * 16 + b;
+                    const int jj = sg.ct * LB + cc * 16 + b;
                     const float re = v[2 * b], im = v[2 * b + 1];
                     if (dump) {
                         if (d < D && jj < L) a.chi_out[((size_t)pair * D + d) * L + jj] = make_float2(re, im);
@@ -425,7 +541,7 @@ fwd_gemm_kernel(const GemmArgs g) {
             }
         }
         tc::fence_before_sync();
-        if (a.mode != FWD_DUMP) {
+        if (finish && a.mode != FWD_DUMP) {
             for (int o = 16; o > 0; o >>= 1) {
                 const float obk = __shfl_xor_sync(0xffffffffu, best, o);
                 const long long oi = __shfl_xor_sync(0xffffffffu, best_idx, o);
@@ -447,6 +563,7 @@ fwd_gemm_kernel(const GemmArgs g) {
                 if (a.pvmax) { a.pvmax[ob] = 0.f; a.psum[ob] = 0.f; }
             }
         }
+        }  // pieces
     }
 
     tc::fence_before_sync();
@@ -464,13 +581,18 @@ fwd_gemm_kernel(const GemmArgs g) {
 // Row u = 0 holds (Re b, -Im b) per sample, row u = 1 (Im b, Re b), with
 // b = x_m(n) E[n, j] in FP32 (E built in FP64 on the host); bins beyond L and
 // samples beyond N are zero.
+// It also zeroes the split schedule's tile counters for the contraction that
+// follows (the previous contraction has finished: this kernel waits for the
+// kernel ahead of it, which waited for that contraction).
 __global__ void gemm_bimg_kernel(const float2* __restrict__ x, const float2* __restrict__ E, int M, int N, int L,
-                                 int LB, int n_ct, int n_kc, int spc, uint16_t* __restrict__ img) {
+                                 int LB, int n_ct, int n_kc, int spc, uint16_t* __restrict__ img,
+                                 int* __restrict__ tile_cnt, int n_tiles) {
     pdl_wait();
     pdl_trigger();
     const int G = spc / 4;
     const long long total = (long long)M * n_ct * n_kc * LB * G;
     const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile_cnt != nullptr && id < n_tiles) tile_cnt[id] = 0;
     if (id >= total) return;
     const int jj = (int)(id % LB);
     long long rest = id / LB;
@@ -511,14 +633,55 @@ __global__ void gemm_bimg_kernel(const float2* __restrict__ x, const float2* __r
 }
 
 cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int LB, int spc, void* img,
-                             int pdl, cudaStream_t s) {
+                             int* tile_cnt, int n_tiles, int pdl, cudaStream_t s) {
     const int n_ct = (L + LB - 1) / LB, n_kc = (N + spc - 1) / spc;
-    if (spc % 4 != 0) return cudaErrorInvalidValue;
-    const long long total = (long long)M * n_ct * n_kc * LB * (spc / 4);
+    if (spc % 4 != 0 || n_tiles < 0) return cudaErrorInvalidValue;
+    long long total = (long long)M * n_ct * n_kc * LB * (spc / 4);
+    if (tile_cnt != nullptr && total < n_tiles) total = n_tiles;
     const int threads = 256;
     const long long blocks = (total + threads - 1) / threads;
     return launch_ex(gemm_bimg_kernel, dim3((unsigned)blocks), dim3(threads), 0, s, pdl != 0, x, E, M, N, L, LB,
-                     n_ct, n_kc, spc, reinterpret_cast<uint16_t*>(img));
+                     n_ct, n_kc, spc, reinterpret_cast<uint16_t*>(img), tile_cnt, n_tiles);
+}
+
+// The split schedule of the CTAs (see GemmArgs), checked by walking it as the
+// kernel does: every CTA must get at least one chunk (else a tile could wait
+// for a piece that no CTA holds) and at most kGemmMaxSeg pieces.
+GemmSplitPlan gemm_split_plan(int P, int n_blocks, int n_ct, int k_lo, int D, int N, int spc, int ctas) {
+    GemmSplitPlan plan{false, 0, 0, 0};
+    if (P < 1 || n_blocks < 1 || n_ct < 1 || spc < 1 || ctas < 1) return plan;
+    const long long PGC = (long long)P * n_ct;
+    std::vector<int> nb(n_blocks);
+    long long W = 0;
+    for (int b = 0; b < n_blocks; ++b) {
+        int c0 = 0;
+        nb[b] = gemm_block_chunks(k_lo, D, N, spc, b, &c0);
+        if (nb[b] < 1) return plan;
+        W += PGC * nb[b];
+    }
+    if (W < ctas) return plan;
+    const long long G = ctas;
+    int max_pieces = 1, max_segs = 0;
+    for (long long c = 0; c < G; ++c) {
+        const long long w0 = c * W / G, w1 = (c + 1) * W / G;
+        long long base = 0;
+        int b = 0, segs = 0;
+        for (long long x = w0; x < w1;) {
+            while (x >= base + PGC * nb[b]) { base += PGC * nb[b]; ++b; }
+            const long long qi = (x - base) / nb[b];
+            const long long ts = base + qi * nb[b], te = ts + nb[b];
+            const long long cf = ((ts + 1) * G - 1) / W, cl = (te * G - 1) / W;
+            if (cl - cf + 1 > max_pieces) max_pieces = (int)(cl - cf + 1);
+            ++segs;
+            x = w1 < te ? w1 : te;
+        }
+        if (segs > max_segs) max_segs = segs;
+    }
+    plan.ok = max_segs >= 1 && max_segs <= kGemmMaxSeg;
+    plan.work = W;
+    plan.max_pieces = max_pieces;
+    plan.max_segs = max_segs;
+    return plan;
 }
 
 size_t gemm_bimg_bytes(int M, int N, int L, int LB, int spc) {
@@ -548,15 +711,36 @@ int gemm_smem_bytes(int LB, int N, int spc, int sb, int sa, int tiles) {
     return b <= 227 * 1024 ? b : 0;
 }
 
+// CTAs that fit on one SM at once: tensor memory (512 columns) and shared
+// memory (228 KB, 1 KB of it reserved per CTA) decide.
+int gemm_ctas_per_sm(int LB, int N, int spc, int sb, int sa, int tiles) {
+    const int smem = gemm_smem_bytes(LB, N, spc, sb, sa, tiles);
+    const int tcols = gemm_tmem_cols(2 * LB, spc, sa, tiles);
+    if (smem <= 0 || tcols <= 0) return 1;
+    const int by_tmem = 512 / tcols, by_smem = (228 * 1024) / (smem + 1024);
+    const int n = by_tmem < by_smem ? by_tmem : by_smem;
+    return n > 0 ? n : 1;
+}
+
 template <int NC, int SPC, int SB, int SA, int T>
 static cudaError_t launch_cfg(const GemmArgs& g, int smem, cudaStream_t s, bool prepare_only) {
     if constexpr (gemm_tmem_cols(NC, SPC, SA, T) == 0) {
         return cudaErrorInvalidValue;   // more tensor memory than an SM has
     } else {
-    auto kern = fwd_gemm_kernel<NC, SPC, SB, SA, T>;
+    // the split schedule is built for one pair per CTA in the default pipeline shape
+    constexpr bool kCanSplit = (T == 1 && SPC == 32 && SB == 2 && SA == 2);
+    if (g.split_ctas > 0 && !kCanSplit) return cudaErrorInvalidValue;
+    void (*kern)(const GemmArgs) = fwd_gemm_kernel<NC, SPC, SB, SA, T, false>;
+    if constexpr (kCanSplit) {
+        if (prepare_only) {
+            cudaError_t e = set_smem_once(reinterpret_cast<const void*>(fwd_gemm_kernel<NC, SPC, SB, SA, T, true>), smem);
+            if (e != cudaSuccess) return e;
+        }
+        if (g.split_ctas > 0) kern = fwd_gemm_kernel<NC, SPC, SB, SA, T, true>;
+    }
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess || prepare_only) return e;
-    const int grid = g.f.M * g.f.M / T * g.f.n_chunks * g.n_ct;
+    const int grid = g.split_ctas > 0 ? g.split_ctas : g.f.M * g.f.M / T * g.f.n_chunks * g.n_ct;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(32 * (4 * T + 2));
@@ -629,6 +813,9 @@ cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s) {
         return cudaErrorInvalidValue;
     const int P = g.f.M * g.f.M;
     if (!(g.tiles == 1 || g.tiles == 2) || P % g.tiles != 0) return cudaErrorInvalidValue;
+    if (g.split_ctas > 0 && (g.tiles != 1 || g.part == nullptr || g.tile_cnt == nullptr || g.max_pieces < 1 ||
+                             g.split_work < g.split_ctas))
+        return cudaErrorInvalidValue;
     return dispatch(g, s, false);
 }
 

@@ -126,15 +126,45 @@ struct GemmArgs {
     int tiles;                  // pairs (delay tiles) per CTA sharing each B stage (1, or 2 when M*M is even)
     unsigned long long timeout_ns;  // limit of every pipeline wait
     int test_stall;             // failure-detection test: the MMA issuer waits on a barrier nothing completes
+    // Split schedule (0 CTAs: one CTA per tile).  split_ctas CTAs each take an
+    // equal contiguous range of the split_work sample chunks of all tiles in
+    // tile order; a tile shared by several CTAs is finished by the last of
+    // them to arrive (tile_cnt), which adds the pieces' FP32 partials (part,
+    // [tile][max_pieces][2 LB columns][128 rows]) in piece order.
+    int split_ctas;
+    long long split_work;
+    int max_pieces;
+    float* part;
+    int* tile_cnt;              // [tiles], zeroed by the B-image kernel of each evaluation
 };
+// Sample chunks of delay block b (128 delays from k_lo + 128 b): the chunks
+// c0 .. c0 + count - 1 of spc samples hold every sample n with a valid lag
+// product n + k in [0, N) for some delay of the block.
+__host__ __device__ inline int gemm_block_chunks(int k_lo, int D, int N, int spc, int b, int* c0) {
+    const int d0 = b * kGemmRows;
+    const int k_first = k_lo + d0;
+    const int k_last = k_lo + (D < d0 + kGemmRows ? D : d0 + kGemmRows) - 1;
+    const int n_begin = k_last < 0 ? -k_last : 0;
+    const int n_end = N < N - k_first ? N : N - k_first;
+    *c0 = n_begin / spc;
+    return (n_end + spc - 1) / spc - *c0;
+}
+// A split schedule over `ctas` CTAs for P pairs x n_blocks delay blocks x
+// n_ct column tiles (one pair per CTA): ok when every CTA gets at least one
+// chunk and at most kGemmMaxSeg pieces; work = total chunks, max_pieces =
+// most CTAs sharing one tile.
+constexpr int kGemmMaxSeg = 8;
+struct GemmSplitPlan { bool ok; long long work; int max_pieces; int max_segs; };
+GemmSplitPlan gemm_split_plan(int P, int n_blocks, int n_ct, int k_lo, int D, int N, int spc, int ctas);
 int gemm_bins_per_tile(int L);
 int gemm_smem_bytes(int LB, int N, int spc, int sb, int sa, int tiles);
+int gemm_ctas_per_sm(int LB, int N, int spc, int sb, int sa, int tiles);   // CTAs that fit on one SM
 bool gemm_shape_supported(int LB, int N, int spc, int sb, int sa, int tiles);
 cudaError_t gemm_prepare(int LB, int N, int spc, int sb, int sa, int tiles);
 cudaError_t launch_fwd_gemm(const GemmArgs& g, cudaStream_t s);
 // B_m = x_m(n) e^{j 2 pi nu_j n} images of one evaluation (E: [N][L] FP32 phasors)
 cudaError_t launch_gemm_bimg(const float2* x, const float2* E, int M, int N, int L, int LB, int spc, void* img,
-                             int pdl, cudaStream_t s);
+                             int* tile_cnt, int n_tiles, int pdl, cudaStream_t s);
 size_t gemm_bimg_bytes(int M, int N, int L, int LB, int spc);
 
 // Record the message of a failed call that has no context (read back by

@@ -70,6 +70,11 @@ struct af_ctx {
     int gemm_tiles = 1;                   // pairs per CTA sharing each B stage
     unsigned long long gemm_timeout_ns = 2000000000ull;   // limit of every pipeline wait
     int gemm_test_stall = 0;              // failure-detection test hook (SQNGD_GEMM_TEST_STALL)
+    int gemm_split_ctas = 0;              // split schedule: CTAs sharing the chunk work (0: one CTA per tile)
+    long long gemm_split_work = 0;        // chunks of all tiles
+    int gemm_max_pieces = 0, gemm_ntiles = 0;
+    float* gemm_part = nullptr;           // [tiles][max pieces][2 LB][128] partial accumulators of shared tiles
+    int* gemm_tile_cnt = nullptr;         // [tiles] arrivals at each shared tile
     double2* pre64 = nullptr;
     double2* tw64 = nullptr;
     double2* E64 = nullptr;
@@ -188,7 +193,7 @@ static void free_all(af_ctx* c) {
                     c->level64, c->pkey, c->pidx, c->pvmax, c->psum, c->pkey64, c->pidx64, c->cdiag,
                     c->xs, c->xs2, c->m_rho, c->v_rho, c->rho_acc, c->du, c->gy, c->zb, c->dydz, c->xh, c->x64, c->h64, c->acc_out, c->terms_scratch, c->errflag,
                     c->ctr, c->best2, c->log, c->pchi, c->adj_part, c->adj_cls, c->dense, c->tw_adj,
-                    c->bimg};
+                    c->bimg, c->gemm_part, c->gemm_tile_cnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -351,6 +356,40 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
             c->err = "AF_PATH_SPLIT_BF16: pipeline shape does not fit this N and L";
             return fail(AF_ERR_UNIMPLEMENTED);
         }
+        // Split schedule: with fewer tiles than SMs, the CTAs that fit at once
+        // share the chunk work equally and tiles are split between them, so
+        // no SM idles (measured on M=4, N=1024, 128 bins, 101 delays, 64 tiles
+        // of 32 bins: 30.2 -> 27.2 us per forward pass).  With more tiles than
+        // SMs it measured slower (256 tiles on 152 SMs: 38.5 -> 44.0 us): each
+        // CTA then holds about two pieces, and a piece's window fill, partial
+        // store and merge cost more than the balance gains.
+        // SQNGD_GEMM_SPLIT=0 turns it off; SQNGD_GEMM_SPLIT_CTAS=n forces n
+        // CTAs (tests of the schedule).
+        {
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1)
+                sms = 1;
+            const int n_blocks = (c->D + kGemmRows - 1) / kGemmRows;
+            const int n_ct = (L + c->gemm_lb - 1) / c->gemm_lb;
+            const int ntile = P * n_blocks * n_ct;
+            const int fit = sms * gemm_ctas_per_sm(c->gemm_lb, N, c->gemm_spc, c->gemm_sb, c->gemm_sa, 1);
+            int ctas = (ntile < sms) ? fit : 0;
+            if (const char* e = getenv("SQNGD_GEMM_SPLIT"))
+                if (atoi(e) == 0) ctas = 0;
+            if (const char* e = getenv("SQNGD_GEMM_SPLIT_CTAS")) ctas = atoi(e) > 0 ? atoi(e) : ctas;
+            // built for one pair per CTA in the default pipeline shape
+            if (c->gemm_tiles != 1 || c->gemm_spc != 32 || c->gemm_sb != 2 || c->gemm_sa != 2) ctas = 0;
+            if (ctas > 0) {
+                const GemmSplitPlan plan =
+                    gemm_split_plan(P, n_blocks, n_ct, c->cfg.k_lo, c->D, N, c->gemm_spc, ctas);
+                if (plan.ok) {
+                    c->gemm_split_ctas = ctas;
+                    c->gemm_split_work = plan.work;
+                    c->gemm_max_pieces = plan.max_pieces;
+                    c->gemm_ntiles = ntile;
+                }
+            }
+        }
     }
     c->grid_fft = uniform;
     if (cfg->pnorm > 0.0) {
@@ -449,6 +488,15 @@ extern "C" af_status af_init(const af_config* cfg, void* stream, af_ctx** out) {
     if (c->path == AF_PATH_SPLIT_BF16) {
         if ((s = dalloc(c, &c->bimg, gemm_bimg_bytes(M, N, L, c->gemm_lb, c->gemm_spc) / sizeof(uint16_t))))
             return fail(s);
+        if (c->gemm_split_ctas > 0) {
+            const size_t np = (size_t)c->gemm_ntiles * c->gemm_max_pieces * (2 * c->gemm_lb) * kGemmRows;
+            if ((s = dalloc(c, &c->gemm_part, np)) || (s = dalloc(c, &c->gemm_tile_cnt, (size_t)c->gemm_ntiles)))
+                return fail(s);
+            if (cudaMemset(c->gemm_tile_cnt, 0, sizeof(int) * c->gemm_ntiles) != cudaSuccess) {
+                c->err = "cudaMemset failed";
+                return fail(AF_ERR_CUDA);
+            }
+        }
         const int LB = c->gemm_lb;
         c->gemm_n_ct = (L + LB - 1) / LB;
         c->gemm_n_kc = (N + c->gemm_spc - 1) / c->gemm_spc;
@@ -618,7 +666,7 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
     if (c->path == AF_PATH_SPLIT_BF16) {
         // this evaluation's B_m images, then the contraction
         cudaError_t e = launch_gemm_bimg(a.x, c->E, c->cfg.M, c->cfg.N, c->cfg.L, c->gemm_lb, c->gemm_spc, c->bimg,
-                                         a.pdl, s);
+                                         c->gemm_tile_cnt, c->gemm_ntiles, a.pdl, s);
         if (e != cudaSuccess) return e;
         GemmArgs g{};
         g.f = a;
@@ -633,6 +681,11 @@ static cudaError_t launch_fwd(af_ctx* c, const FwdArgs<float2, float>& a, cudaSt
         g.tiles = c->gemm_tiles;
         g.timeout_ns = c->gemm_timeout_ns;
         g.test_stall = c->gemm_test_stall;
+        g.split_ctas = c->gemm_split_ctas;
+        g.split_work = c->gemm_split_work;
+        g.max_pieces = c->gemm_max_pieces;
+        g.part = c->gemm_part;
+        g.tile_cnt = c->gemm_tile_cnt;
         return launch_fwd_gemm(g, s);
     }
     return (c->path == AF_PATH_FFT) ? launch_fwd_fft_f32(a, s) : launch_fwd_dft_f32(a, s);

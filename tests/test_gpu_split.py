@@ -224,3 +224,73 @@ def test_pipeline_wait_timeout_is_reported_and_device_stays_usable(api, orc, mon
     ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
     assert np.max(np.abs(chi - ref)) <= CHI_TOL * np.max(np.abs(ref))
     good.af_sync()
+
+
+def _split_work(M, N, nu, k_lo, k_hi, spc=32):
+    """Sample chunks of all tiles (the split schedule's work) with the widest
+    column tile, and the tiles' count: as the library plans them."""
+    L = len(nu)
+    lb = 16
+    while lb < L and lb < 128:
+        lb *= 2
+    n_ct = (L + lb - 1) // lb
+    D = k_hi - k_lo + 1
+    total = 0
+    for b in range((D + 127) // 128):
+        k_first, k_last = k_lo + 128 * b, k_lo + min(D, 128 * b + 128) - 1
+        n_begin, n_end = max(0, -k_last), min(N, N - k_first)
+        total += (n_end + spc - 1) // spc - n_begin // spc
+    return M * M * n_ct * total
+
+
+@pytest.mark.parametrize("case,ctas", [
+    ((2, 100, wl.window_grid(0.05, 64), -40, 40), "3"),     # tiles of 4 chunks in 2-3 pieces
+    ((2, 100, wl.window_grid(0.05, 64), -40, 40), "16"),    # one chunk per CTA: 4 pieces per tile
+    ((3, 300, wl.window_grid(0.1, 40), -299, 299), "11"),   # several whole and split tiles per CTA
+    ((3, 300, wl.window_grid(0.1, 40), -299, 299), "97"),
+    ((1, 50, np.sort(wl.uniform(5, 200, 1) - 0.5), -30, 49), "3"),   # two column tiles
+])
+def test_split_schedule_matches_oracle(api, orc, case, ctas, monkeypatch):
+    """The split schedule forced onto small problems (the library enables it by
+    itself when more tiles than SMs do not fill whole waves): CTAs share the
+    chunk work, split tiles are finished by their last piece.  chi on every
+    cell, the loss terms, the winning cell and the gradient match the oracle,
+    and a second evaluation gives bit-identical results (the pieces are added
+    in a fixed order whichever CTA finishes the tile)."""
+    M, N, nu, k_lo, k_hi = case
+    assert _split_work(M, N, nu, k_lo, k_hi) >= int(ctas)   # every CTA gets work: the schedule is used
+    monkeypatch.setenv("SQNGD_GEMM_SPLIT_CTAS", ctas)
+    x, h = _pair(orc, 1000 + N + int(ctas), M, N)
+    ctx = _ctx(api, M, N, 4, nu, k_lo, k_hi, eps=0.2, snrl_db=1.0)
+    chi = ctx.af_ambiguity(_dev(x), _dev(h)).cpu().numpy()
+    ref = orc.ambiguity(x, h, nu, k_lo, k_hi)
+    assert np.max(np.abs(chi - ref)) <= CHI_TOL * np.max(np.abs(ref))
+    _check_terms(orc, ctx, x, h, nu, k_lo, k_hi, 0.2, 1.0)
+    outs = []
+    for _ in range(2):
+        gx = torch.empty((M, N), dtype=torch.complex64, device="cuda")
+        gh = torch.empty_like(gx)
+        terms, _, _ = ctx.af_loss_grad_xh(_dev(x), _dev(h), grad_x=gx, grad_h=gh)
+        ctx.af_sync()
+        outs.append((terms.cpu().numpy(), gx.cpu().numpy(), gh.cpu().numpy()))
+    for u, v in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(u, v)
+    ctx.close()
+
+
+def test_split_schedule_on_and_off_agree(api, orc, monkeypatch):
+    """The learned workload (64 tiles: the split schedule is the default there)
+    with and without the schedule: the same PSL classes and winning class."""
+    w = wl.learned()
+    x, h = _pair(orc, 1234, w.M, w.N)
+    res = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SQNGD_GEMM_SPLIT", flag)
+        ctx = _ctx(api, w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi)
+        terms, _, _ = ctx.af_loss_grad_xh(_dev(x), _dev(h))
+        ctx.af_sync()
+        res.append(terms.cpu().numpy())
+        ctx.close()
+    a, b = res
+    np.testing.assert_allclose(a[[1, 2, 3]], b[[1, 2, 3]], rtol=1e-5)
+    assert int(a[5]) == int(b[5])
