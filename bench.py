@@ -52,9 +52,10 @@ def _args():
                    help="none: only the headline step, its roofline and e2e (profiler launch lists)")
     p.add_argument("--no-time-to-target", action="store_true",
                    help="skip the time-to-PSL-target experiment (run on rank 0 of a 1-GPU run by default)")
-    p.add_argument("--fwd-path", default="fft", choices=["fft", "fft-mid", "split", "corr", "adj"],
+    p.add_argument("--fwd-path", default="fft", choices=["fft", "fft-mid", "split", "split-learned", "corr", "adj"],
                    help="with --fwd-only: fft = the differentiation workload on the FFT path, fft-mid = the mid "
-                        "workload, split = the narrow-window workload on the tensor-core path, corr = the "
+                        "workload, split = the narrow-window workload on the tensor-core path, split-learned = the "
+                        "learned workload on that path (its split schedule), corr = the "
                         "zero-Doppler correlation setting (L = 1), adj = whole p-norm evaluations (forward, dense "
                         "adjoint, finish) on the differentiation workload")
     p.add_argument("--fwd-only", type=int, default=0,
@@ -639,8 +640,8 @@ def _fwd_only(args, api, wl, dev):
     """N launches of one forward kernel on its workload (profiler captures)."""
     import torch
     path = args.fwd_path
-    if path == "split":
-        w = wl.precision()
+    if path in ("split", "split-learned"):
+        w = wl.precision() if path == "split" else wl.learned()
         ctx = api.Context(w.M, w.N, w.B, w.nu, w.k_lo, w.k_hi, path=api.AF_PATH_SPLIT_BF16)
     elif path == "corr":
         w = wl.correlation()
