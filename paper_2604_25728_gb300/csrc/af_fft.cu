@@ -204,6 +204,41 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
             // the instruction-cache lines.
             auto scan = [&](auto weighted) {
                 const float* wrow = a.wmap + (size_t)d * L + t;
+                if constexpr (!decltype(weighted)::value && sizeof(K) == 4 && (RL * NBL) % 8 == 0) {
+                    // Uniform weights: the thread's cells in scan order (increasing
+                    // cell index) in groups of 8.  A group only matters if its
+                    // largest key beats the best so far, and then its first
+                    // maximal cell is the candidate -- the same cell as a
+                    // cell-by-cell scan with a strict comparison.
+                    constexpr int GS = 8;
+#pragma unroll
+                    for (int g0 = 0; g0 < RL * NBL; g0 += GS) {
+                        K key[GS];
+#pragma unroll
+                        for (int q = 0; q < GS; ++q) {
+                            const C c = v[((g0 + q) % NBL) * RL + (g0 + q) / NBL];
+                            key[q] = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
+                        }
+                        K gm = key[0];
+#pragma unroll
+                        for (int q = 1; q < GS; ++q) gm = fmaxf(gm, key[q]);
+                        if (gm > best) {
+                            // compile-time register indices only (a run-time index
+                            // would move v to local memory)
+                            int off = TPR * ((g0 + GS - 1) % NBL) + ((g0 + GS - 1) / NBL) * NSL;
+                            C cs = v[((g0 + GS - 1) % NBL) * RL + (g0 + GS - 1) / NBL];
+#pragma unroll
+                            for (int q = GS - 2; q >= 0; --q)
+                                if (key[q] == gm) {
+                                    off = TPR * ((g0 + q) % NBL) + ((g0 + q) / NBL) * NSL;
+                                    cs = v[((g0 + q) % NBL) * RL + (g0 + q) / NBL];
+                                }
+                            best = gm;
+                            best_li = lbase + off;
+                            best_c = cs;
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int r = 0; r < RL; ++r) {
 #pragma unroll
@@ -217,6 +252,7 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                         }
                         if (key > best) { best = key; best_li = lbase + off; best_c = c; }
                     }
+                }
                 }
                 if constexpr (MODE == MODE_REDUCE_PNORM) {
                     // the p-norm partial of this thread's cells of the row: their
