@@ -53,6 +53,64 @@ __host__ __device__ constexpr int fft_smem_entries(int N, int rpc) {
     return fold_len<L>(N) * 2 + rpc + Plan<L, E>::tw_len + (NT / (L / E)) * Plan<L, E>::padlen;
 }
 
+// The last pass of a 2048-point row at 32 values per thread (passes 32, 32,
+// 2; the row's 64 threads are two warps).  After pass 1, lane l of warp h
+// holds in register r the element l + 32 r + 1024 h, so the radix-2
+// butterfly x = l + 32 r (NS = 1024) pairs register r of lane l in the two
+// warps.  Warp 0 takes r < 16 and warp 1 r >= 16: each warp hands its
+// partner lane the 16 registers the partner keeps -- half the data of a full
+// exchange -- through warp-uniform branches with compile-time register
+// indices.  Leaves y(x) in v[q] and y(x + 1024) in v[16 + q] for
+// x = l + 32 (q + 16 h).
+template <typename C>
+__device__ __forceinline__ void last_pass_pair(C (&v)[32], int t, int slot, C* buf, const C* tw_last) {
+    const int l = t & 31, h = t >> 5;
+    C w[16];
+    if (h == 0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[q * 64 + l] = v[16 + q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) buf[q * 64 + 32 + l] = v[q];
+    }
+    row_sync<64>(slot);
+    if (h == 0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] = buf[q * 64 + 32 + l];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] = buf[q * 64 + l];
+    }
+    row_sync<64>(slot);
+    if (h == 0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const C b = cmul(w[q], tw_last[l + 32 * q]);
+            const C a = v[q];
+            v[q] = cadd(a, b);
+            v[16 + q] = csub(a, b);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const C b = cmul(v[16 + q], tw_last[l + 32 * (16 + q)]);
+            const C a = w[q];
+            v[q] = cadd(a, b);
+            v[16 + q] = csub(a, b);
+        }
+    }
+}
+
+// Cell i (0 <= i < E) of a thread's row after the last pass, in increasing
+// bin order: its register and its bin relative to the thread's first bin.
+template <int E, int TPR, int RL, int NBL, int NSL, bool PAIR>
+struct CellMap {
+    static __device__ __forceinline__ constexpr int reg(int i) { return PAIR ? i : (i % NBL) * RL + i / NBL; }
+    static __device__ __forceinline__ constexpr int off(int i) {
+        return PAIR ? 32 * (i % 16) + 1024 * (i / 16) : TPR * (i % NBL) + (i / NBL) * NSL;
+    }
+};
+
 // FP32 CTAs of 256 threads keep to 128 registers, so that two fit on an SM
 // when their shared memory allows.
 template <int L, int E, int NT, int MODE, typename C, typename K>
@@ -64,6 +122,9 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
     constexpr int TPR = PL::T;               // threads per row
     constexpr int RS = kThreads / TPR;       // row slots per CTA
     constexpr int RL = PL::radix(PL::passes - 1), NSL = PL::ns(PL::passes - 1), NBL = E / RL;
+    // rows of 2048 bins at 32 values per thread: the paired last pass
+    constexpr bool kPair = (sizeof(C) == sizeof(float2) && L == 2048 && E == 32 && PL::passes == 3 && TPR == 64);
+    using CM = CellMap<E, TPR, RL, NBL, NSL, kPair>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N;
     const int XS = fold_len<L>(N);
@@ -185,25 +246,34 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
             }
         }
         pass_compute<L, E, E, 1>(v, t, tws);
-        fft_rest<L, E, 1>(v, t, slot, buf, tws);
+        if constexpr (kPair) {
+            pass_store<L, E, E, 1>(v, t, buf);
+            row_sync<TPR>(slot);
+            pass_load<L, E, E>(v, t, buf);
+            row_sync<TPR>(slot);
+            pass_compute<L, E, E, E>(v, t, tws + PL::tw_off(1));
+            last_pass_pair(v, t, slot, buf, tws + PL::tw_off(2));
+        } else {
+            fft_rest<L, E, 1>(v, t, slot, buf, tws);
+        }
+        // this thread's first bin; cell i is bin cbase + CM::off(i), in v[CM::reg(i)]
+        const int cbase = kPair ? (t & 31) + 512 * (t >> 5) : t;
 
         // ---- epilogue: chi(k, bin) is in registers, bins in increasing order ----
         if constexpr (MODE == MODE_DUMP) {
             if (row_in) {
-                C* out = a.chi_out + ((size_t)pair * a.D + d) * L + t;
+                C* out = a.chi_out + ((size_t)pair * a.D + d) * L + cbase;
 #pragma unroll
-                for (int r = 0; r < RL; ++r)
-#pragma unroll
-                    for (int s = 0; s < NBL; ++s) out[TPR * s + r * NSL] = v[s * RL + r];
+                for (int i = 0; i < E; ++i) out[CM::off(i)] = v[CM::reg(i)];
             }
         } else if (row_in && !(auto_pair && k == 0)) {
-            const int lbase = (d - d_begin) * L + t;
+            const int lbase = (d - d_begin) * L + cbase;
             // The weighted scan is a separate copy of the loop: with the weight
             // test inside the unrolled loop the uniform path's instructions are
             // interleaved with the weighted ones and the hot loop spans twice
             // the instruction-cache lines.
             auto scan = [&](auto weighted) {
-                const float* wrow = a.wmap + (size_t)d * L + t;
+                const float* wrow = a.wmap + (size_t)d * L + cbase;
                 if constexpr (!decltype(weighted)::value && sizeof(K) == 4 && (RL * NBL) % 8 == 0) {
                     // Uniform weights: the thread's cells in scan order (increasing
                     // cell index) in groups of 8.  A group only matters if its
@@ -216,7 +286,7 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                         K key[GS];
 #pragma unroll
                         for (int q = 0; q < GS; ++q) {
-                            const C c = v[((g0 + q) % NBL) * RL + (g0 + q) / NBL];
+                            const C c = v[CM::reg(g0 + q)];
                             key[q] = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
                         }
                         K gm = key[0];
@@ -225,13 +295,13 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                         if (gm > best) {
                             // compile-time register indices only (a run-time index
                             // would move v to local memory)
-                            int off = TPR * ((g0 + GS - 1) % NBL) + ((g0 + GS - 1) / NBL) * NSL;
-                            C cs = v[((g0 + GS - 1) % NBL) * RL + (g0 + GS - 1) / NBL];
+                            int off = CM::off(g0 + GS - 1);
+                            C cs = v[CM::reg(g0 + GS - 1)];
 #pragma unroll
                             for (int q = GS - 2; q >= 0; --q)
                                 if (key[q] == gm) {
-                                    off = TPR * ((g0 + q) % NBL) + ((g0 + q) / NBL) * NSL;
-                                    cs = v[((g0 + q) % NBL) * RL + (g0 + q) / NBL];
+                                    off = CM::off(g0 + q);
+                                    cs = v[CM::reg(g0 + q)];
                                 }
                             best = gm;
                             best_li = lbase + off;
@@ -240,18 +310,15 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                     }
                 } else {
 #pragma unroll
-                for (int r = 0; r < RL; ++r) {
-#pragma unroll
-                    for (int s = 0; s < NBL; ++s) {
-                        const int off = TPR * s + r * NSL;
-                        const C c = v[s * RL + r];
-                        K key = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
-                        if constexpr (decltype(weighted)::value) {
-                            const float w = __ldg(wrow + off);
-                            key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
-                        }
-                        if (key > best) { best = key; best_li = lbase + off; best_c = c; }
+                for (int i = 0; i < E; ++i) {
+                    const int off = CM::off(i);
+                    const C c = v[CM::reg(i)];
+                    K key = (K)c.x * (K)c.x + (K)c.y * (K)c.y;
+                    if constexpr (decltype(weighted)::value) {
+                        const float w = __ldg(wrow + off);
+                        key = (w > 0.f) ? (a.weight_mode == WM_MAP ? (K)w * (K)w * key : key) : (K)-1;
                     }
+                    if (key > best) { best = key; best_li = lbase + off; best_c = c; }
                 }
                 }
                 if constexpr (MODE == MODE_REDUCE_PNORM) {
@@ -260,17 +327,15 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                     // then sum (key/pv)^hp with no branch per cell
                     float kmax = -1.f;
 #pragma unroll
-                    for (int r = 0; r < RL; ++r)
-#pragma unroll
-                        for (int s = 0; s < NBL; ++s) {
-                            const C c = v[s * RL + r];
-                            float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
-                            if constexpr (decltype(weighted)::value) {
-                                const float w = __ldg(wrow + TPR * s + r * NSL);
-                                key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : -1.f;
-                            }
-                            kmax = fmaxf(kmax, key);
+                    for (int i = 0; i < E; ++i) {
+                        const C c = v[CM::reg(i)];
+                        float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
+                        if constexpr (decltype(weighted)::value) {
+                            const float w = __ldg(wrow + CM::off(i));
+                            key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : -1.f;
                         }
+                        kmax = fmaxf(kmax, key);
+                    }
                     if (kmax > pv) {
                         ps = (pv > 0.f) ? ps * exp2f(a.half_p * __log2f(pv / kmax)) : 0.f;
                         pv = kmax;
@@ -279,18 +344,16 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                     if (pv > 0.f) {
                         float acc = 0.f;
 #pragma unroll
-                        for (int r = 0; r < RL; ++r)
-#pragma unroll
-                            for (int s = 0; s < NBL; ++s) {
-                                const C c = v[s * RL + r];
-                                float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
-                                if constexpr (decltype(weighted)::value) {
-                                    const float w = __ldg(wrow + TPR * s + r * NSL);
-                                    key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : 0.f;
-                                }
-                                // key = 0 gives log2 = -inf and a zero term
-                                acc += ex2_approx(a.half_p * __log2f(key * ipv));
+                        for (int i = 0; i < E; ++i) {
+                            const C c = v[CM::reg(i)];
+                            float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
+                            if constexpr (decltype(weighted)::value) {
+                                const float w = __ldg(wrow + CM::off(i));
+                                key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : 0.f;
                             }
+                            // key = 0 gives log2 = -inf and a zero term
+                            acc += ex2_approx(a.half_p * __log2f(key * ipv));
+                        }
                         ps += acc;
                     }
                 }

@@ -182,10 +182,12 @@ def test_loss_and_gradient_dft(api, orc, case):
     _check_terms(orc, api, ctx, x, h, nu, k_lo, k_hi, 0.2, 1.0)
 
 
-def test_loss_with_weight_map(api, orc):
-    M, N, L = 2, 48, 64
+@pytest.mark.parametrize("M,N,L,k_lo,k_hi", [
+    (2, 48, 64, -47, 47),
+    (2, 160, 2048, -60, 70),     # 2048-bin rows: the paired last pass of the 32-value transform
+])
+def test_loss_with_weight_map(api, orc, M, N, L, k_lo, k_hi):
     nu = wl.full_grid(L)
-    k_lo, k_hi = -47, 47
     D = k_hi - k_lo + 1
     wts = (wl.uniform(9, D * L, 3).reshape(D, L) / N).astype(np.float32)
     wts[:, :5] = 0.0                      # cells outside the ROI
