@@ -10,10 +10,11 @@
 // products are formed in registers without bounds checks.  The row is
 // transformed by a Stockham FFT with E values per thread (T = L/E threads per
 // row, radix E passes then the remainder, exchanges through a padded shared
-// buffer).  The last pass leaves chi in registers, where the sidelobe
-// reduction of Eqs. 7-9 runs: per-CTA max of w^2|chi|^2 with its lowest
-// linear cell index, plus p-norm partials.  chi is never written to memory
-// in the reduce modes.
+// buffer; at L = 2048, E = 32 the last radix-2 pass is paired across the
+// row's two warps and exchanges half the data).  The last pass leaves chi in
+// registers, where the sidelobe reduction of Eqs. 7-9 runs: per-CTA max of
+// w^2|chi|^2 with its lowest linear cell index, plus p-norm partials.  chi
+// is never written to memory in the reduce modes.
 //
 // This replaces the zero-padded FFT correlation of Eq. 36 (Doppler-major:
 // one FFT pair per Doppler bin) with a delay-major transform: one L-point FFT
