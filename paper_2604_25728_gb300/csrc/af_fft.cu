@@ -88,16 +88,16 @@ __device__ __forceinline__ void last_pass_pair(C (&v)[32], int t, int slot, C* b
         for (int q = 0; q < 16; ++q) {
             const C b = cmul(w[q], tw_last[l + 32 * q]);
             const C a = v[q];
-            v[q] = cadd(a, b);
-            v[16 + q] = csub(a, b);
+            v[q] = padd(a, b);
+            v[16 + q] = psub(a, b);
         }
     } else {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const C b = cmul(v[16 + q], tw_last[l + 32 * (16 + q)]);
             const C a = w[q];
-            v[q] = cadd(a, b);
-            v[16 + q] = csub(a, b);
+            v[q] = padd(a, b);
+            v[16 + q] = psub(a, b);
         }
     }
 }
