@@ -224,10 +224,11 @@ __global__ void __launch_bounds__(NT, 1) adj_fft_kernel(const AdjArgs a) {
                     const C gt = v[s * RL + r];
                     if (NF == 1) {
                         const int n = t + TPR * q;
-                        // h_l(n+k) from the window (zero outside [0, N)); conj(G2) h
-                        gxr[q] = cadd(gxr[q], cmul(cconj(gt), hk[TPR * q]));
+                        // h_l(n+k) from the window (zero outside [0, N)); conj(G2) h, added
+                        // into the accumulators by fused multiply-adds
+                        gxr[q] = cmac_conj(gxr[q], gt, hk[TPR * q]);
                         const int p = n + k;
-                        if (p >= 0 && p < N) gh_slot[p] = cadd(gh_slot[p], cmul(gt, xk[TPR * q]));
+                        if (p >= 0 && p < N) gh_slot[p] = cmac(gh_slot[p], gt, xk[TPR * q]);
                     } else {
                         for (int c = 0; c < NF; ++c) {
                             const int n = t + TPR * q + c * L;

@@ -28,6 +28,13 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
     return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+// acc + a b and acc + conj(a) b, each as four fused multiply-adds
+template <typename C> __device__ __forceinline__ C cmac(C acc, C a, C b) {
+    return mk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+template <typename C> __device__ __forceinline__ C cmac_conj(C acc, C a, C b) {
+    return mk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
 
 // 2^x by the hardware's approximate base-2 exponential (PTX ex2.approx, results
 // below the normal range flushed to zero): for the per-cell terms of the
