@@ -91,8 +91,13 @@ def _workload():
     return wl.differentiation()
 
 
+def _workload_desc(w) -> str:
+    """The workload as both arms name it in config.workload."""
+    return w.name + ", one outer iteration (20 loss+grad evals) per step"
+
+
 def _config(w, extra=None):
-    cfg = {"workload": w.name + ": one SQNGD outer iteration (10 filter + 10 transmit loss+grad evals) per step",
+    cfg = {"workload": _workload_desc(w),
            "M": w.M, "N": w.N, "B": w.B, "L": w.L, "delays": w.D, "r_n": w.r_n, "c": w.c, "eps": w.eps,
            "snrl_db": w.snrl_db, "evals_per_step": w.n_h + w.n_x,
            "l2": "flushed between timed steps (256 MiB memset outside each step's events)"}
@@ -572,7 +577,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name + ", one outer iteration (20 loss+grad evals) per step",
+            "config": {"workload": _workload_desc(w),
                        "path": "FFT", "l2": "flushed between steps (256 MiB memset)"},
             "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
             "cpu_baseline": cpu and {k: cpu[k] for k in ("value", "unit", "cores", "kind")} | {
