@@ -343,19 +343,36 @@ fwd_fft_kernel(const FwdArgs<C, K> a) {
                         ipv = 1.f / kmax;
                     }
                     if (pv > 0.f) {
-                        float acc = 0.f;
+                        // (key/pv)^(p/2): p = 8 and 16 by squaring, other p by the
+                        // hardware base-2 exponential and logarithm; one copy of the
+                        // cell loop per kind (a uniform branch, none per cell)
+                        auto sum_terms = [&](auto kind) {
+                            constexpr int PK = decltype(kind)::value;
+                            float acc = 0.f;
 #pragma unroll
-                        for (int i = 0; i < E; ++i) {
-                            const C c = v[CM::reg(i)];
-                            float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
-                            if constexpr (decltype(weighted)::value) {
-                                const float w = __ldg(wrow + CM::off(i));
-                                key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : 0.f;
+                            for (int i = 0; i < E; ++i) {
+                                const C c = v[CM::reg(i)];
+                                float key = (float)c.x * (float)c.x + (float)c.y * (float)c.y;
+                                if constexpr (decltype(weighted)::value) {
+                                    const float w = __ldg(wrow + CM::off(i));
+                                    key = (w > 0.f) ? (a.weight_mode == WM_MAP ? w * w * key : key) : 0.f;
+                                }
+                                const float r = key * ipv;
+                                if constexpr (PK == 4) {
+                                    const float r2 = r * r;
+                                    acc += r2 * r2;
+                                } else if constexpr (PK == 8) {
+                                    const float r2 = r * r, r4 = r2 * r2;
+                                    acc += r4 * r4;
+                                } else {
+                                    acc += ex2_approx(a.half_p * __log2f(r));   // key = 0: log2 = -inf, a zero term
+                                }
                             }
-                            // key = 0 gives log2 = -inf and a zero term
-                            acc += ex2_approx(a.half_p * __log2f(key * ipv));
-                        }
-                        ps += acc;
+                            return acc;
+                        };
+                        if (a.half_p == 4.f) ps += sum_terms(std::integral_constant<int, 4>{});
+                        else if (a.half_p == 8.f) ps += sum_terms(std::integral_constant<int, 8>{});
+                        else ps += sum_terms(std::integral_constant<int, 0>{});
                     }
                 }
             };
