@@ -28,6 +28,12 @@
 //              no-swizzle K-major layout) with cp.async.bulk.
 // Stages are double-buffered with mbarriers; every wait is bounded and a
 // timeout sets bit 1 of the error flag and ends the kernel cleanly.
+//
+// With fewer tiles than SMs a second instantiation runs the split schedule:
+// the CTAs that fit at once each take an equal range of the sample chunks of
+// all tiles, cut into pieces at tile boundaries, and a tile shared by several
+// CTAs is finished by the last of them to arrive (an atomic ticket; no CTA
+// waits for another), which adds the pieces' FP32 partials in piece order.
 #include <cuda_bf16.h>
 
 #include <vector>
